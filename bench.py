@@ -1,0 +1,361 @@
+#!/usr/bin/env python
+"""Benchmark: gradient Gcell-updates/s of the superposition adjoint method.
+
+One step = one full wave_adjoint_sensitivity call over the workload (all
+shots: forward, superposed backward pass, sensitivity, misfit).  One gradient
+cell-update = one cell advanced one time step in both passes, so a step is
+worth sum_s ncells * N_s units.
+
+Default workload: 3D 512^3, 8th order, layered velocity, 16 shots with record
+lengths 1500-2500 (the batched multi-shot configuration).  Inputs are resident
+in HBM before the timed region; the state of one shot (2 x 537 MB) and the
+coefficient and accumulator grids are each larger than the 129 MB L2.
+
+`--impl reference` times the FP64 CPU oracle on a bounded sample of the same
+workload (the reference arm); it never touches the GPU.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "gradient Gcell-updates/s (fwd+adjoint+sens), % HBM roofline, batched vs plain"
+UNIT = "Gcell-updates/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="w2", choices=["w0", "w1", "w2", "w3", "w4"])
+    ap.add_argument("--mode", default="auto", choices=["auto", "plain", "batched"])
+    ap.add_argument("--kahan", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-plain", action="store_true", help="skip the plain-path comparison")
+    return ap.parse_args()
+
+
+def make_workload(name):
+    from paper_2509_15744_gb300 import workloads as WL
+    return {"w0": WL.workload0, "w1": WL.workload1, "w2": WL.workload2, "w3": WL.workload3,
+            "w4": WL.workload4}[name]()
+
+
+def units_of(wl):
+    return float(sum(wl.ncells * n for n in wl.nt))
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle sample (cpu_baseline leg and the reference arm)
+# ---------------------------------------------------------------------------
+def oracle_sample(wl, crop=160, nt=2):
+    """Run the oracle's Algorithm 1 (one shot, nt steps) on a crop of the
+    workload and return (gradient cell-updates/s, description)."""
+    import numpy as np
+    import oracle as O
+
+    shape = tuple(min(crop, s) for s in wl.shape)
+    sl = tuple(slice(0, s) for s in shape)
+    param = np.ascontiguousarray(np.asarray(wl.init_param)[sl]).astype(np.float64)
+    dt = O.cfl_dt(wl.h, wl.vmax, wl.ndim, wl.order, wl.cfl_fraction)
+    med = O.Medium(wl.physics, param, wl.h, dt, wl.order, wl.bc)
+    size = int(np.prod(shape))
+    mid = [s // 2 for s in shape]
+    mid[0] = min(2, shape[0] - 1)
+    src = int(np.ravel_multi_index(tuple(mid), shape))
+    rec = np.arange(0, shape[-1], 2, dtype=np.int64)
+    wav = np.ones(nt + 1)
+    shot = O.Shot(src, wav, rec, np.zeros((len(rec), nt + 1)), 1.0)
+    t0 = time.perf_counter()
+    O.superposition_gradient(med, [shot], nt, 1.0)
+    el = time.perf_counter() - t0
+    desc = f"oracle Algorithm 1 (FP64 numpy, one shot, {nt} steps each way) on a {'x'.join(map(str, shape))} crop"
+    return size * nt / el / 1e9, desc, el
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    wl = make_workload(args.workload)
+    crop = 192 if wl.ndim == 3 else 2048
+    rates = []
+    desc = ""
+    for i in range(args.warmup + args.steps):
+        r, desc, _ = oracle_sample(wl, crop=crop, nt=6)
+        if i >= args.warmup:
+            rates.append(r)
+    value = statistics.median(rates)
+    out = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": wl.name, "sample": desc},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), float(parts[3]), parts[5:9]))
+            except ValueError:
+                continue
+        if not rows:
+            return None
+        sm = [r[0] for r in rows]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for n, v in zip(names, r[3]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(r[1] for r in rows),
+                "power_w_max": max(r[2] for r in rows), "samples": len(rows), "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def measured_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def kernel_traffic(kernel_file, workload_name):
+    """dram bytes per launch of the step kernel from the committed ncu summary,
+    if it was taken on the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "step_kernel_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    src = open(os.path.join(ROOT, "paper_2509_15744_gb300", "csrc", kernel_file), "rb").read()
+    digest = hashlib.sha256(src).hexdigest()[:16]
+    vals = {}
+    for line in open(path):
+        if ":" in line:
+            k, v = line.split(":", 1)
+            vals[k.strip()] = v.strip()
+    if vals.get("kernel_source_sha256_16") != digest or vals.get("workload") != workload_name:
+        return None
+    try:
+        return float(vals["dram_bytes_per_launch_full_size"])
+    except (KeyError, ValueError):
+        return None
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import numpy as np
+    import torch
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    import __graft_entry__ as ge
+    ge.build()
+    from paper_2509_15744_gb300 import wave as W
+
+    wl = make_workload(args.workload)
+    dt = W.cfl_dt(wl.ndim, wl.order, wl.h, wl.vmax, wl.cfl_fraction)
+    mode = "plain" if args.mode in ("auto", "plain") else "batched"
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+
+    # ---- inputs resident in HBM --------------------------------------------
+    param0 = torch.from_numpy(np.ascontiguousarray(wl.init_param, dtype=np.float32)).to(dev)
+    wk = {"ricker": "ricker", "sine_burst": "sine_burst"}[wl.wavelet.kind]
+    wavs = [W.wavelet(wk, wl.wavelet.freq, dt, n, nc=wl.wavelet.nc, psi0=wl.wavelet.psi0, device=dev)
+            for n in wl.nt]
+    recs = [torch.from_numpy(r).to(dev) for r in wl.receivers]
+    observed = [None] * wl.nshots
+    if wl.objective == "l2":
+        ptrue = torch.from_numpy(np.ascontiguousarray(wl.true_param, dtype=np.float32)).to(dev)
+        mtrue = W.Model(ptrue, wl.h, dt, wl.order, wl.physics, wl.bc)
+        for i in range(wl.nshots):
+            observed[i] = mtrue.forward([W.Shot(wl.sources[i], wavs[i], recs[i])])[0]
+        del mtrue, ptrue
+    shots = [W.Shot(wl.sources[i], wavs[i], recs[i], observed[i]) for i in range(wl.nshots)]
+    model = W.Model(param0, wl.h, dt, wl.order, wl.physics, wl.bc, kahan=args.kahan)
+    gkw = dict(objective=wl.objective, patch_sign=wl.patch_sign, batched=(mode == "batched"))
+
+    # ---- warm-up -----------------------------------------------------------
+    for _ in range(args.warmup):
+        model.gradient(shots, **gkw)
+    barrier()
+
+    # ---- timed region (device-resident inputs) -------------------------------
+    clocks = ClockSampler(local)
+    clocks.start()
+    launches0 = W.launch_count()
+    W.timing_enable(True)
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    e0.record(stream)
+    for _ in range(args.steps):
+        grad, mis, kd = model.gradient(shots, **gkw)
+    e1.record(stream)
+    barrier()
+    ms = e0.elapsed_time(e1)
+    step_ms, step_launches, step_bytes = W.timing_read()
+    W.timing_enable(False)
+    launches = W.launch_count() - launches0
+    clk = clocks.stop()
+    if dist is not None:
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    units = units_of(wl) * world
+    value = units * args.steps / (ms / 1e3) / 1e9
+    grad_norm = float(torch.linalg.vector_norm(grad.double()).item())
+    misfit_val = float(mis.item())
+
+    # ---- plain single-shot-at-a-time path on the same GPU (two shots) ---------
+    plain = None
+    if mode == "batched" and not args.no_plain:
+        sub = shots[:2]
+        model.gradient(sub, objective=wl.objective, patch_sign=wl.patch_sign)
+        barrier()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        model.gradient(sub, objective=wl.objective, patch_sign=wl.patch_sign)
+        b.record(stream)
+        barrier()
+        pu = float(sum(wl.ncells * n for n in wl.nt[:2]))
+        plain = {"value": pu / (a.elapsed_time(b) / 1e3) / 1e9, "unit": UNIT, "shots": 2}
+
+    # ---- end to end through the public API with host buffers ------------------
+    e2e = None
+    if not args.no_e2e:
+        h_param = torch.from_numpy(np.ascontiguousarray(wl.init_param, dtype=np.float32)).pin_memory()
+        h_obs = [o.cpu().pin_memory() if o is not None else None for o in observed]
+        h_wav = [w.cpu().pin_memory() for w in wavs]
+        h_rec = [r.cpu().pin_memory() for r in recs]
+        h_grad = torch.empty(wl.init_param.shape, dtype=torch.float32).pin_memory()
+        h_mis = torch.empty(1, dtype=torch.float64).pin_memory()
+        h2d = h_param.numel() * 4 + sum(o.numel() * 4 for o in h_obs if o is not None) + \
+            sum(w.numel() * 4 for w in h_wav) + sum(r.numel() * 8 for r in h_rec)
+        d2h = h_grad.numel() * 4 + 8
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            p = h_param.to(dev, non_blocking=True)
+            sh = [W.Shot(wl.sources[i], h_wav[i].to(dev, non_blocking=True), h_rec[i].to(dev, non_blocking=True),
+                         h_obs[i].to(dev, non_blocking=True) if h_obs[i] is not None else None)
+                  for i in range(wl.nshots)]
+            m2 = W.Model(p, wl.h, dt, wl.order, wl.physics, wl.bc, kahan=args.kahan)
+            g2, mi2, _ = m2.gradient(sh, **gkw)
+            h_grad.copy_(g2, non_blocking=True)
+            h_mis.copy_(mi2, non_blocking=True)
+            torch.cuda.synchronize()
+        barrier()
+        el = time.perf_counter() - t0
+        if dist is not None:
+            t = torch.tensor([el], device=dev, dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            el = float(t.item())
+        e2e = {"value": units * args.steps / el / 1e9, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h)}
+
+    # ---- roofline of the dominant kernel (the fused step) ---------------------
+    peak, peak_kind = measured_peak()
+    achieved = step_bytes / (step_ms / 1e3) / 1e9 if step_ms > 0 else 0.0
+    kfile = "step_velocity.cu" if wl.physics == "velocity" else "step_density.cu"
+    traffic = kernel_traffic(kfile, wl.name)
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "peak_source": peak_kind,
+                "traffic": traffic,
+                "algorithmic_bytes_per_launch": step_bytes / max(step_launches, 1),
+                "kernel": kfile.replace(".cu", ""), "launches": step_launches,
+                "avg_launch_ms": step_ms / max(step_launches, 1),
+                "kernel_share_of_step": step_ms / ms if ms > 0 else None}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        r, desc, _ = oracle_sample(wl, crop=192 if wl.ndim == 3 else 2048, nt=6)
+        cpu = {"value": r, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc}
+
+    if rank == 0:
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": wl.name, "shape": list(wl.shape), "order": wl.order, "physics": wl.physics,
+                       "shots": wl.nshots, "nt_total": int(sum(wl.nt)), "mode": mode, "kahan": args.kahan,
+                       "storage": "f32", "parallelism": f"replicas x{world}",
+                       "l2": "inputs larger than L2 (each resident grid > 129 MB)"},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "gpu_launches": int(launches),
+            "plain": plain, "check": {"misfit": misfit_val, "grad_l2": grad_norm, "k": float(kd.item())},
+        }
+        print(json.dumps(out), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

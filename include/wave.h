@@ -1,0 +1,217 @@
+/*
+ * wave.h -- C ABI of libwave: memory-efficient adjoint (superposition) gradients
+ * of the acoustic wave equation on one GB300 (sm_103a).
+ *
+ * Method: arXiv 2509.15744 (Herrmann, Buerchner, Kollmannsberger), "A Memory
+ * Efficient Adjoint Method to Enable Billion Parameter Optimization on a Single
+ * GPU in Dynamic Problems".  Sec. 2 states the forward problems (Eq.
+ * scalarwaveequation in squared-slowness form, Eq. wavetopopt), sources
+ * (Eq. source1, Eq. source2), objectives (Eq. cost1, Eq. cost2), adjoint
+ * sources (Eq. adjointSource1, Eq. adjointSource2) and Frechet kernels
+ * (Eq. kernel1, Eq. kernel2).  Sec. 3.1 gives the leapfrog stencils (Eq.
+ * FDstencil1, Eq. FDstencil2).  Sec. 4 gives the superposed field (Eq.
+ * superposedPDE, Eq. superposedforce), the approximation K~ = (K(u^s,u^s) -
+ * K(u,u)) / 2k (Eq. superposedkernel) and Algorithm 1.
+ *
+ * General conventions
+ *  - Grids are dense, C order, x fastest: cell (x, y, z) has flat index
+ *    (z * ny + y) * nx + x.  In 2D nz = 1.
+ *  - Pointers named *_dev are device pointers owned by the caller.  The library
+ *    never allocates device memory: every call that needs scratch takes a
+ *    caller workspace whose size the matching *_workspace_size call returns.
+ *    Workspace must be 256-byte aligned.
+ *  - All calls that take a stream enqueue their work on it and return without
+ *    waiting, except where stated (wave_model_create reads back one number).
+ *    Host-side validation happens before anything is enqueued; on a non-OK
+ *    return nothing has been enqueued unless the status is WAVE_ECUDA.
+ *  - No C++ exception crosses this boundary.  Every call returns wave_status.
+ *  - The stencil state is FP32 (or BF16/FP16 storage of the resident time
+ *    levels); the sensitivity accumulates in FP32 (optionally Kahan-
+ *    compensated); FP64 is used only for the misfit and norm reductions.
+ */
+#ifndef WAVE_H
+#define WAVE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  WAVE_OK = 0,
+  WAVE_EINVAL = 1,        /* bad argument (sizes, indices, null pointer, order) */
+  WAVE_EUNSTABLE = 2,     /* dt violates the leapfrog stability bound */
+  WAVE_EWORKSPACE = 3,    /* workspace too small or misaligned */
+  WAVE_ECUDA = 4,         /* a CUDA runtime call failed; see wave_last_error() */
+  WAVE_ETIMEOUT = 5,      /* a bounded device wait gave up */
+  WAVE_ENONFINITE = 6,    /* non-finite value detected */
+  WAVE_EUNSUPPORTED = 7   /* valid request this build does not implement */
+} wave_status;
+
+typedef enum {
+  WAVE_VELOCITY = 0,  /* param = v [m/s]; mass m = 1/v^2, order-p Laplacian (Eq. scalarwaveequation, squared-slowness form) */
+  WAVE_DENSITY = 1    /* param = gamma in [0,1]; kappa^-1, rho^-1 linear in gamma (Sec. 2.3, Eq. wavetopopt); order 2 only */
+} wave_physics;
+
+typedef enum {
+  WAVE_DIRICHLET = 0, /* odd mirror about the virtual wall nodes -1 and n */
+  WAVE_NEUMANN = 1    /* even mirror about the half cell (Eq. BC, ghost cells of Sec. 3.1) */
+} wave_bc;
+
+typedef enum {
+  WAVE_F32 = 0,       /* resident time levels stored in FP32 */
+  WAVE_BF16 = 1,      /* stored in BF16, stencil arithmetic in FP32 */
+  WAVE_F16 = 2        /* stored in FP16, stencil arithmetic in FP32 */
+} wave_storage;
+
+typedef enum {
+  WAVE_OBJ_L2 = 0,    /* C = 1/2 dt sum_n sum_r (u_r^n - d_r^n)^2 (Eq. cost1, rectangle rule over levels 0..N) */
+  WAVE_OBJ_PATCH = 1  /* C = sign dt/n_s sum_n sum_{i in patch} (u_i^n)^2 (Eq. cost2; receivers = patch cells) */
+} wave_objective;
+
+typedef enum {
+  WAVE_SUPERPOSITION = 0, /* Algorithm 1: K~ = (K(u^s,u^s) - K(u,u)) / 2k, memory independent of N */
+  WAVE_EXACT_STORED = 1   /* standard adjoint over the stored forward history (comparator; memory ~ N grids) */
+} wave_grad_mode;
+
+typedef enum {
+  WAVE_GRAD_MASS = 0,  /* dC/dm (velocity: m = 1/v^2) or dC/dgamma (density) */
+  WAVE_GRAD_PARAM = 1  /* dC/dv (velocity) or dC/dgamma (density) */
+} wave_grad_wrt;
+
+/* Grid and discretisation.  n[0] = nx (fastest), n[1] = ny, n[2] = nz (1 in 2D).
+ * Each axis needs n >= order + 1 cells. */
+typedef struct {
+  int32_t ndim;        /* 2 or 3 */
+  int32_t order;       /* 2, 4, 6 or 8 (velocity); 2 (density) */
+  int64_t n[3];
+  double h;            /* grid spacing [m] */
+  double dt;           /* time step [s] */
+  int32_t physics;     /* wave_physics */
+  int32_t bc;          /* wave_bc */
+  int32_t storage;     /* wave_storage */
+  int32_t kahan;       /* 1: Kahan-compensated sensitivity accumulation */
+} wave_grid_desc;
+
+/* One shot: a Kronecker point source (Eq. source1) and its receivers.
+ * wavelet_dev: psi(t_n), t_n = n dt, n = 0..nt (sample 0 is never used).
+ * rec_cells_dev: flat cell indices; an out-of-range index is skipped (its trace
+ *   and residual are zero, nothing is injected there).
+ * observed_dev: [nrec][nt+1] measured traces (level n at column n), or NULL
+ *   for zero data (the patch objective).
+ * traces_dev: [nrec][nt+1] output of wave_forward (ignored by the gradient). */
+typedef struct {
+  int64_t src_cell;
+  int32_t nt;          /* N_s: levels 0..N_s are recorded */
+  int32_t nrec;
+  const float* wavelet_dev;
+  const int64_t* rec_cells_dev;
+  const float* observed_dev;
+  float* traces_dev;
+} wave_shot;
+
+typedef struct {
+  int32_t objective;   /* wave_objective */
+  int32_t mode;        /* wave_grad_mode */
+  int32_t batched;     /* 0: shots one after another; 1: all shots advanced together */
+  int32_t grad_wrt;    /* wave_grad_wrt */
+  double patch_sign;   /* +1 suppress / -1 amplify (Sec. 5.2 sign flip); patch objective only */
+  double k;            /* superposition factor (Eq. superposedforce); <= 0 selects it automatically */
+  double k_ratio;      /* automatic k = k_ratio * ||psi|| / ||f_adj|| of the first shot; 0 -> 1e-2 */
+} wave_gradient_opts;
+
+typedef struct wave_model_s* wave_model;
+
+/* ---- version, errors --------------------------------------------------- */
+const char* wave_status_string(wave_status s);
+/* Text of the last CUDA error seen by this thread (empty if none). */
+const char* wave_last_error(void);
+/* Number of kernels this library has launched in this process. */
+uint64_t wave_launch_count(void);
+
+/* ---- step-kernel timing ------------------------------------------------------
+ * When enabled, every launch of the fused step kernel is bracketed by CUDA
+ * events on its stream.  wave_timing_read waits for the recorded events and
+ * returns the summed kernel time, the number of timed launches and their
+ * algorithmic bytes (per cell: read u^n, u^{n-1}, coef [+ b], write u^{n+1},
+ * [+ accumulator RMW, + compensation RMW]).  Enabling resets the counters.
+ * Not thread-safe; not for use under stream capture. */
+wave_status wave_timing_enable(int32_t on);
+wave_status wave_timing_read(double* step_ms, uint64_t* step_launches, double* step_bytes);
+
+/* ---- stability ----------------------------------------------------------
+ * dt at `fraction` of the leapfrog limit for a homogeneous medium of speed
+ * vmax: dt = fraction * 2h / (vmax sqrt(ndim S)), S = |c_0 + 2 sum (-1)^j c_j|
+ * of the order-p central second-derivative weights (Sec. 3.1 stencil family).
+ * Returns 0 on invalid input. */
+double wave_cfl_dt(int32_t ndim, int32_t order, double h, double vmax, double fraction);
+
+/* ---- source time functions ---------------------------------------------
+ * Fills out_dev[0..nt] with psi(n dt).  kind 0: Ricker, (1 - 2 pi^2 f^2 tau^2)
+ * exp(-pi^2 f^2 tau^2), tau = t - 1/f.  kind 1: sine burst of Eq. source2,
+ * psi0 sin(w t) sin^2(w t / 2 n_c) for t <= 2 pi n_c / w, w = 2 pi f. */
+wave_status wave_wavelet(int32_t kind, double freq, int32_t nc, double psi0, double dt,
+                         int32_t nt, float* out_dev, void* stream);
+
+/* ---- model ---------------------------------------------------------------
+ * A model holds the per-cell coefficients derived from param (Eq. FDstencil1/2
+ * prefactors) in a caller workspace of wave_model_workspace_size() bytes.
+ * param_dev: dense [nz][ny][nx] FP32 (v in m/s, or gamma).  It must stay valid
+ * while the model is used (the dC/dv chain rule reads it).  Create checks the
+ * stability bound on the device and waits for that one number
+ * (WAVE_EUNSTABLE if violated).  Destroy frees only the host handle. */
+wave_status wave_model_workspace_size(const wave_grid_desc* desc, size_t* bytes);
+wave_status wave_model_create(const wave_grid_desc* desc, const float* param_dev,
+                              void* workspace_dev, size_t ws_bytes, void* stream,
+                              wave_model* out);
+wave_status wave_model_destroy(wave_model model);
+/* Tuning hook (used by the autotuner): the number of rows (2D) or planes (3D)
+ * that one warp (2D) or CTA (3D) of the step kernel marches over.  Any value
+ * >= 1 is valid; it changes speed, never results. */
+wave_status wave_model_set_block(wave_model model, int64_t zblock);
+wave_status wave_model_get_block(wave_model model, int64_t* zblock);
+
+/* ---- forward ---------------------------------------------------------------
+ * Leapfrog u^{n+1} = 2u^n - u^{n-1} + dt^2/a (L u^n + f^n) for n = 1..N_s with
+ * traces of levels 0..N_s written to each shot's traces_dev.
+ * init_dev: NULL for u^0 = u^1 = 0 (Eq. IC), else dense {u^0, u^1} (2 grids).
+ * final_dev: NULL, or dense output {u^N, u^{N+1}} of the last shot. */
+wave_status wave_forward_workspace_size(wave_model model, const wave_shot* shots, int32_t nshots,
+                                        size_t* bytes);
+wave_status wave_forward(wave_model model, const wave_shot* shots, int32_t nshots,
+                         const float* init_dev, float* final_dev,
+                         void* workspace_dev, size_t ws_bytes, void* stream);
+
+/* ---- gradient (Algorithm 1) -----------------------------------------------
+ * Superposition mode: per shot, forward N_s steps (plus one unrecorded step to
+ * N_s + 1) accumulating -K(u,u), form the adjoint source f_adj^n = -w (u_r^n -
+ * d_r^n) (Eq. adjointSource1/2), then run the superposed field u^s = u + k u_adj
+ * backward from (u^{N+1}, u^N) with force f + k f_adj (Eq. superposedforce)
+ * accumulating +K(u^s,u^s); K~ = difference / 2k (Eq. superposedkernel).
+ * grad_dev: dense FP32 grid, summed over shots, w.r.t. opts->grad_wrt.
+ * misfit_dev: one double, C summed over shots.  k_dev: one double, the k used
+ * (all shots share it).  Exact mode stores the forward history instead and
+ * returns the standard adjoint gradient. */
+wave_status wave_gradient_workspace_size(wave_model model, const wave_shot* shots, int32_t nshots,
+                                         const wave_gradient_opts* opts, size_t* bytes);
+wave_status wave_adjoint_sensitivity(wave_model model, const wave_shot* shots, int32_t nshots,
+                                     const wave_gradient_opts* opts, float* grad_dev,
+                                     double* misfit_dev, double* k_dev,
+                                     void* workspace_dev, size_t ws_bytes, void* stream);
+
+/* ---- misfit ----------------------------------------------------------------
+ * out_dev[0] = 0.5 * weight * dt * sum_i (syn_i - obs_i)^2 in FP64 over count
+ * FP32 samples (Eq. cost1 with the rectangle rule); obs_dev may be NULL (zero).
+ * Deterministic two-pass reduction through caller scratch of
+ * wave_misfit_scratch_size(count) bytes. */
+size_t wave_misfit_scratch_size(int64_t count);
+wave_status misfit(const float* syn_dev, const float* obs_dev, int64_t count, double dt,
+                   double weight, double* out_dev, void* scratch_dev, size_t scratch_bytes,
+                   void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* WAVE_H */

@@ -1,0 +1,646 @@
+// Host side of libwave: argument validation, workspace carving and the time
+// loop of Algorithm 1 (Sec. 4) over the fused kernels.  All work is enqueued
+// on the caller's stream; the only host wait is the stability check of
+// wave_model_create.  No device memory is allocated here.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "wave_internal.cuh"
+
+using namespace wave;
+
+namespace wave {
+uint64_t launches();
+}
+
+static thread_local std::string g_last_error;
+
+#define CUDA_TRY(expr)                                            \
+  do {                                                            \
+    cudaError_t _e = (expr);                                      \
+    if (_e != cudaSuccess) {                                      \
+      g_last_error = std::string(#expr) + ": " + cudaGetErrorString(_e); \
+      return WAVE_ECUDA;                                          \
+    }                                                             \
+  } while (0)
+
+// ---------------------------------------------------------------------------
+// workspace carving: the same walk computes sizes (base == nullptr) and
+// pointers, 256-byte aligned.
+// ---------------------------------------------------------------------------
+struct Carve {
+  char* base;
+  size_t off = 0;
+  explicit Carve(void* b) : base(static_cast<char*>(b)) {}
+  template <typename T>
+  T* take(size_t count) {
+    off = (off + 255) & ~size_t(255);
+    T* p = base ? reinterpret_cast<T*>(base + off) : nullptr;
+    off += count * sizeof(T);
+    return p;
+  }
+  void* take_bytes(size_t bytes) { return take<char>(bytes); }
+};
+
+static size_t storage_bytes(int storage) { return storage == WAVE_F32 ? 4 : 2; }
+
+// Central second-derivative weights c_0..c_r (Sec. 3.1 family, textbook values).
+static const double kWeights[4][5] = {
+    {-2.0, 1.0, 0, 0, 0},
+    {-5.0 / 2.0, 4.0 / 3.0, -1.0 / 12.0, 0, 0},
+    {-49.0 / 18.0, 3.0 / 2.0, -3.0 / 20.0, 1.0 / 90.0, 0},
+    {-205.0 / 72.0, 8.0 / 5.0, -1.0 / 5.0, 8.0 / 315.0, -1.0 / 560.0}};
+
+static double symbol_max(int order) {
+  const int r = order / 2;
+  double s = kWeights[r - 1][0];
+  for (int j = 1; j <= r; ++j) s += 2.0 * ((j & 1) ? -1.0 : 1.0) * kWeights[r - 1][j];
+  return fabs(s);
+}
+
+// Material derivatives of the acoustic model (Sec. 2.3).
+static const double kDa = 1.0 / 6.87e8 - 1.0 / 1.419e5;   // d kappa^-1 / d gamma
+static const double kDb = 1.0 / 2643.0 - 1.0 / 1.204;     // d rho^-1 / d gamma
+
+struct wave_model_s {
+  wave_grid_desc d;
+  Geom g;
+  const float* param;
+  float* coef;
+  float* bmat;
+  int64_t zblock;
+  double stability;
+};
+
+static wave_status validate_desc(const wave_grid_desc* d) {
+  if (!d) return WAVE_EINVAL;
+  if (d->ndim != 2 && d->ndim != 3) return WAVE_EINVAL;
+  if (d->order != 2 && d->order != 4 && d->order != 6 && d->order != 8) return WAVE_EINVAL;
+  if (d->physics != WAVE_VELOCITY && d->physics != WAVE_DENSITY) return WAVE_EINVAL;
+  if (d->bc != WAVE_DIRICHLET && d->bc != WAVE_NEUMANN) return WAVE_EINVAL;
+  if (d->storage < WAVE_F32 || d->storage > WAVE_F16) return WAVE_EINVAL;
+  if (!(d->h > 0.0) || !(d->dt > 0.0)) return WAVE_EINVAL;
+  for (int a = 0; a < d->ndim; ++a)
+    if (d->n[a] < d->order + 1) return WAVE_EINVAL;
+  if (d->ndim == 2 && d->n[2] != 1) return WAVE_EINVAL;
+  if (d->physics == WAVE_DENSITY && d->order != 2) return WAVE_EINVAL;
+  if (d->physics == WAVE_DENSITY && d->ndim != 2) return WAVE_EUNSUPPORTED;
+  return WAVE_OK;
+}
+
+static Geom make_geom(const wave_grid_desc* d) {
+  Geom g;
+  g.ndim = d->ndim;
+  g.r = d->order / 2;
+  g.bc = d->bc;
+  g.nx = d->n[0];
+  g.ny = d->n[1];
+  g.nz = d->ndim == 3 ? d->n[2] : 1;
+  g.px = (g.nx + kStrip - 1) / kStrip * kStrip;
+  g.plane = g.px * g.ny;
+  g.cells = g.plane * g.nz;
+  return g;
+}
+
+static int64_t default_zblock(const Geom& g) {
+  const int64_t nstrips = (g.nx + kStrip - 1) / kStrip;
+  if (g.ndim == 2) {
+    // about 24 warps per SM over 152 SMs
+    int64_t by = nstrips * g.ny / (152 * 24);
+    return std::max<int64_t>(8, std::min<int64_t>(by, 256));
+  }
+  return std::min<int64_t>(64, g.nz);
+}
+
+extern "C" {
+
+const char* wave_status_string(wave_status s) {
+  switch (s) {
+    case WAVE_OK: return "ok";
+    case WAVE_EINVAL: return "invalid argument";
+    case WAVE_EUNSTABLE: return "time step violates the leapfrog stability bound";
+    case WAVE_EWORKSPACE: return "workspace too small or misaligned";
+    case WAVE_ECUDA: return "CUDA error";
+    case WAVE_ETIMEOUT: return "bounded device wait timed out";
+    case WAVE_ENONFINITE: return "non-finite value";
+    case WAVE_EUNSUPPORTED: return "not supported by this build";
+  }
+  return "unknown status";
+}
+
+const char* wave_last_error(void) { return g_last_error.c_str(); }
+
+uint64_t wave_launch_count(void) { return wave::launches(); }
+
+double wave_cfl_dt(int32_t ndim, int32_t order, double h, double vmax, double fraction) {
+  if ((ndim != 2 && ndim != 3 && ndim != 1) || (order != 2 && order != 4 && order != 6 && order != 8)) return 0.0;
+  if (!(h > 0) || !(vmax > 0) || !(fraction > 0)) return 0.0;
+  return fraction * 2.0 * h / (vmax * sqrt(ndim * symbol_max(order)));
+}
+
+wave_status wave_wavelet(int32_t kind, double freq, int32_t nc, double psi0, double dt, int32_t nt, float* out_dev,
+                         void* stream) {
+  if ((kind != 0 && kind != 1) || !(freq > 0) || !(dt > 0) || nt < 0 || !out_dev) return WAVE_EINVAL;
+  if (kind == 1 && nc < 1) return WAVE_EINVAL;
+  CUDA_TRY(launch_wavelet(kind, freq, nc, psi0, dt, nt, out_dev, (cudaStream_t)stream));
+  return WAVE_OK;
+}
+
+// ---------------------------------------------------------------------------
+// model
+// ---------------------------------------------------------------------------
+static void carve_model(Carve& c, const Geom& g, int physics, float** coef, float** bmat, float** part,
+                        float** maxv) {
+  *coef = c.take<float>(g.cells);
+  *bmat = physics == WAVE_DENSITY ? c.take<float>(g.cells) : nullptr;
+  *part = c.take<float>(1024);
+  *maxv = c.take<float>(1);
+}
+
+wave_status wave_model_workspace_size(const wave_grid_desc* desc, size_t* bytes) {
+  wave_status st = validate_desc(desc);
+  if (st != WAVE_OK) return st;
+  if (!bytes) return WAVE_EINVAL;
+  Geom g = make_geom(desc);
+  Carve c(nullptr);
+  float *a, *b, *p, *m;
+  carve_model(c, g, desc->physics, &a, &b, &p, &m);
+  *bytes = c.off;
+  return WAVE_OK;
+}
+
+wave_status wave_model_create(const wave_grid_desc* desc, const float* param_dev, void* workspace_dev,
+                              size_t ws_bytes, void* stream, wave_model* out) {
+  wave_status st = validate_desc(desc);
+  if (st != WAVE_OK) return st;
+  if (!param_dev || !out || !workspace_dev) return WAVE_EINVAL;
+  if (reinterpret_cast<uintptr_t>(workspace_dev) % 256) return WAVE_EWORKSPACE;
+  size_t need = 0;
+  wave_model_workspace_size(desc, &need);
+  if (ws_bytes < need) return WAVE_EWORKSPACE;
+  cudaStream_t s = (cudaStream_t)stream;
+  Geom g = make_geom(desc);
+  Carve c(workspace_dev);
+  float *coef, *bmat, *part, *maxv;
+  carve_model(c, g, desc->physics, &coef, &bmat, &part, &maxv);
+  double sym;
+  if (desc->physics == WAVE_VELOCITY) {
+    CUDA_TRY(launch_coef_velocity(g, param_dev, (float)(desc->dt / desc->h), coef, s));
+    sym = desc->ndim * symbol_max(desc->order);
+  } else {
+    CUDA_TRY(launch_coef_density(g, param_dev, desc->dt * desc->dt / (desc->h * desc->h), coef, bmat, s));
+    sym = 0.0;
+  }
+  const int nparts = 1024;
+  CUDA_TRY(launch_stability(g, desc->physics, sym, coef, bmat, part, nparts, s));
+  CUDA_TRY(launch_max_final(part, nparts, maxv, s));
+  float host_max = 0.f;
+  CUDA_TRY(cudaMemcpyAsync(&host_max, maxv, sizeof(float), cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  if (!(host_max <= 4.0f * (1.0f + 1e-5f))) return WAVE_EUNSTABLE;
+  wave_model_s* m = new wave_model_s;
+  m->d = *desc;
+  m->g = g;
+  m->param = param_dev;
+  m->coef = coef;
+  m->bmat = bmat;
+  m->zblock = default_zblock(g);
+  m->stability = host_max;
+  *out = m;
+  return WAVE_OK;
+}
+
+wave_status wave_model_destroy(wave_model model) {
+  delete model;
+  return WAVE_OK;
+}
+
+// Tuning hook: rows (2D) or planes (3D) that one warp / CTA marches over.
+wave_status wave_model_set_block(wave_model model, int64_t zblock) {
+  if (!model || zblock < 1) return WAVE_EINVAL;
+  model->zblock = zblock;
+  return WAVE_OK;
+}
+
+wave_status wave_model_get_block(wave_model model, int64_t* zblock) {
+  if (!model || !zblock) return WAVE_EINVAL;
+  *zblock = model->zblock;
+  return WAVE_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// shared pieces of the time loops
+// ---------------------------------------------------------------------------
+static wave_status validate_shots(const wave_model_s* m, const wave_shot* shots, int32_t nshots, bool need_traces) {
+  if (!shots || nshots < 1) return WAVE_EINVAL;
+  const int64_t total = m->g.nx * m->g.ny * m->g.nz;
+  for (int s = 0; s < nshots; ++s) {
+    const wave_shot& sh = shots[s];
+    if (sh.nt < 1 || sh.nrec < 0) return WAVE_EINVAL;
+    if (sh.src_cell < 0 || sh.src_cell >= total) return WAVE_EINVAL;
+    if (!sh.wavelet_dev) return WAVE_EINVAL;
+    if (sh.nrec > 0 && !sh.rec_cells_dev) return WAVE_EINVAL;
+    if (need_traces && sh.nrec > 0 && !sh.traces_dev) return WAVE_EINVAL;
+  }
+  return WAVE_OK;
+}
+
+static int64_t pitched_cell(const Geom& g, int64_t flat) { return (flat / g.nx) * g.px + flat % g.nx; }
+
+static StepArgs step_args(const wave_model_s* m, const void* cur, void* prev) {
+  StepArgs a;
+  memset(&a, 0, sizeof(a));
+  a.g = m->g;
+  a.u_cur = cur;
+  a.u_prev = prev;
+  a.coef = m->coef;
+  a.bmat = m->bmat;
+  a.da = m->d.physics == WAVE_DENSITY ? (float)kDa : 1.f;
+  a.dbs = m->d.physics == WAVE_DENSITY ? (float)(m->d.dt * m->d.dt / (m->d.h * m->d.h) * kDb) : 0.f;
+  a.zblock = m->zblock;
+  return a;
+}
+
+// ---- optional per-launch timing of the step kernel (CUDA events on the
+// launching stream), read back by wave_timing_read ----------------------------
+struct StepTiming {
+  bool on = false;
+  std::vector<cudaEvent_t> ev;
+  size_t used = 0;
+  double bytes = 0.0;      // algorithmic bytes of the timed launches
+  uint64_t launches = 0;
+};
+static StepTiming g_timing;
+
+static double step_bytes(const wave_model_s* m, const StepArgs& a) {
+  const double cells = (double)(m->g.nx * m->g.ny * m->g.nz);
+  const double eb = (double)storage_bytes(m->d.storage);
+  double b = 3.0 * eb + 4.0;                    // read u^n, u^{n-1}, coef; write u^{n+1}
+  if (m->d.physics == WAVE_DENSITY) b += 4.0;   // read b
+  if (a.acc_mass || a.acc_stiff) b += a.comp ? 16.0 : 8.0;  // accumulator (+ compensation) RMW
+  return cells * b;
+}
+
+static cudaError_t run_step(const wave_model_s* m, const StepArgs& a, cudaStream_t s) {
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (g_timing.on) {
+    while (g_timing.ev.size() < g_timing.used + 2) {
+      cudaEvent_t e;
+      cudaError_t err = cudaEventCreate(&e);
+      if (err != cudaSuccess) return err;
+      g_timing.ev.push_back(e);
+    }
+    e0 = g_timing.ev[g_timing.used];
+    e1 = g_timing.ev[g_timing.used + 1];
+    g_timing.used += 2;
+    cudaEventRecord(e0, s);
+  }
+  cudaError_t err = m->d.physics == WAVE_VELOCITY ? launch_step_velocity(a, m->d.order, m->d.storage, s)
+                                                  : launch_step_density(a, m->d.storage, s);
+  if (g_timing.on) {
+    cudaEventRecord(e1, s);
+    g_timing.bytes += step_bytes(m, a);
+    g_timing.launches += 1;
+  }
+  return err;
+}
+
+extern "C" wave_status wave_timing_enable(int32_t on) {
+  g_timing.on = on != 0;
+  g_timing.used = 0;
+  g_timing.bytes = 0.0;
+  g_timing.launches = 0;
+  return WAVE_OK;
+}
+
+extern "C" wave_status wave_timing_read(double* step_ms, uint64_t* step_launches, double* step_bytes_total) {
+  if (!step_ms || !step_launches || !step_bytes_total) return WAVE_EINVAL;
+  double total = 0.0;
+  for (size_t i = 0; i + 1 < g_timing.used; i += 2) {
+    CUDA_TRY(cudaEventSynchronize(g_timing.ev[i + 1]));
+    float ms = 0.f;
+    CUDA_TRY(cudaEventElapsedTime(&ms, g_timing.ev[i], g_timing.ev[i + 1]));
+    total += ms;
+  }
+  *step_ms = total;
+  *step_launches = g_timing.launches;
+  *step_bytes_total = g_timing.bytes;
+  return WAVE_OK;
+}
+
+static SparseArgs sparse_args(const wave_model_s* m, const int64_t* recp, int32_t nrec) {
+  SparseArgs a;
+  memset(&a, 0, sizeof(a));
+  a.rec_p = recp;
+  a.nrec = nrec;
+  a.glevel = -1;
+  a.src_p = -1;
+  a.ilevel = 0;
+  a.coef = m->coef;
+  a.h2 = (float)(m->d.h * m->d.h);
+  return a;
+}
+
+// ---------------------------------------------------------------------------
+// forward
+// ---------------------------------------------------------------------------
+static void carve_forward(Carve& c, const wave_model_s* m, const wave_shot* shots, int32_t nshots, void** u0,
+                          void** u1, int64_t** recp) {
+  int32_t maxrec = 1;
+  for (int s = 0; s < nshots; ++s) maxrec = std::max(maxrec, shots[s].nrec);
+  const size_t eb = storage_bytes(m->d.storage);
+  *u0 = c.take_bytes(m->g.cells * eb);
+  *u1 = c.take_bytes(m->g.cells * eb);
+  *recp = c.take<int64_t>(maxrec);
+}
+
+extern "C" wave_status wave_forward_workspace_size(wave_model m, const wave_shot* shots, int32_t nshots,
+                                                   size_t* bytes) {
+  if (!m || !bytes) return WAVE_EINVAL;
+  wave_status st = validate_shots(m, shots, nshots, false);
+  if (st != WAVE_OK) return st;
+  Carve c(nullptr);
+  void *u0, *u1;
+  int64_t* recp;
+  carve_forward(c, m, shots, nshots, &u0, &u1, &recp);
+  *bytes = c.off;
+  return WAVE_OK;
+}
+
+extern "C" wave_status wave_forward(wave_model m, const wave_shot* shots, int32_t nshots, const float* init_dev,
+                                    float* final_dev, void* ws, size_t ws_bytes, void* stream) {
+  if (!m) return WAVE_EINVAL;
+  wave_status st = validate_shots(m, shots, nshots, true);
+  if (st != WAVE_OK) return st;
+  size_t need = 0;
+  wave_forward_workspace_size(m, shots, nshots, &need);
+  if (!ws || ws_bytes < need || reinterpret_cast<uintptr_t>(ws) % 256) return WAVE_EWORKSPACE;
+  cudaStream_t s = (cudaStream_t)stream;
+  const Geom& g = m->g;
+  const int stor = m->d.storage;
+  const size_t eb = storage_bytes(stor);
+  Carve c(ws);
+  void *ua, *ub;
+  int64_t* recp;
+  carve_forward(c, m, shots, nshots, &ua, &ub, &recp);
+  const int64_t ncells = g.nx * g.ny * g.nz;
+  for (int si = 0; si < nshots; ++si) {
+    const wave_shot& sh = shots[si];
+    const int N = sh.nt;
+    CUDA_TRY(launch_pitch_indices(g, sh.rec_cells_dev, sh.nrec, recp, s));
+    if (init_dev) {
+      CUDA_TRY(launch_dense_to_pitched(g, init_dev, ua, stor, s));
+      CUDA_TRY(launch_dense_to_pitched(g, init_dev + ncells, ub, stor, s));
+    } else {
+      CUDA_TRY(cudaMemsetAsync(ua, 0, g.cells * eb, s));
+      CUDA_TRY(cudaMemsetAsync(ub, 0, g.cells * eb, s));
+    }
+    SparseArgs sp = sparse_args(m, recp, sh.nrec);
+    sp.traces = sh.traces_dev;
+    sp.tr_ld = N + 1;
+    sp.gsrc = ua;
+    sp.glevel = 0;
+    CUDA_TRY(launch_sparse(sp, stor, s));
+    sp.gsrc = ub;
+    sp.glevel = 1;
+    sp.dst = ua;
+    sp.src_p = pitched_cell(g, sh.src_cell);
+    sp.wavelet = sh.wavelet_dev;
+    sp.ilevel = 1;
+    CUDA_TRY(launch_sparse(sp, stor, s));
+    void* prev = ua;  // u^{n-1}
+    void* cur = ub;   // u^n
+    for (int n = 1; n <= N; ++n) {
+      StepArgs a = step_args(m, cur, prev);
+      CUDA_TRY(run_step(m, a, s));
+      std::swap(prev, cur);  // cur = u^{n+1}, prev = u^n
+      if (n + 1 <= N) {
+        sp.gsrc = cur;
+        sp.glevel = n + 1;
+        sp.dst = prev;
+        sp.ilevel = n + 1;
+        CUDA_TRY(launch_sparse(sp, stor, s));
+      }
+    }
+    if (final_dev && si == nshots - 1) {
+      CUDA_TRY(launch_pitched_to_dense(g, prev, final_dev, stor, s));
+      CUDA_TRY(launch_pitched_to_dense(g, cur, final_dev + ncells, stor, s));
+    }
+  }
+  return WAVE_OK;
+}
+
+// ---------------------------------------------------------------------------
+// gradient (Algorithm 1)
+// ---------------------------------------------------------------------------
+struct GradWs {
+  float* acc;
+  float* comp;
+  void* u0;
+  void* u1;
+  float* resid;
+  int64_t* recp;
+  double* parts;
+  double* scal;  // [0] k, [1] psi2, [2] e2
+};
+
+static void carve_gradient(Carve& c, const wave_model_s* m, const wave_shot* shots, int32_t nshots, GradWs* w) {
+  int64_t maxres = 1;
+  int32_t maxrec = 1;
+  for (int s = 0; s < nshots; ++s) {
+    maxres = std::max<int64_t>(maxres, (int64_t)(shots[s].nt + 1) * shots[s].nrec);
+    maxrec = std::max(maxrec, shots[s].nrec);
+  }
+  const size_t eb = storage_bytes(m->d.storage);
+  w->acc = c.take<float>(m->g.cells);
+  w->comp = m->d.kahan ? c.take<float>(m->g.cells) : nullptr;
+  w->u0 = c.take_bytes(m->g.cells * eb);
+  w->u1 = c.take_bytes(m->g.cells * eb);
+  w->resid = c.take<float>(maxres);
+  w->recp = c.take<int64_t>(maxrec);
+  w->parts = c.take<double>(1024);
+  w->scal = c.take<double>(4);
+}
+
+static wave_status validate_opts(const wave_model_s* m, const wave_gradient_opts* o) {
+  if (!o) return WAVE_EINVAL;
+  if (o->objective != WAVE_OBJ_L2 && o->objective != WAVE_OBJ_PATCH) return WAVE_EINVAL;
+  if (o->mode != WAVE_SUPERPOSITION && o->mode != WAVE_EXACT_STORED) return WAVE_EINVAL;
+  if (o->grad_wrt != WAVE_GRAD_MASS && o->grad_wrt != WAVE_GRAD_PARAM) return WAVE_EINVAL;
+  if (o->mode == WAVE_EXACT_STORED) return WAVE_EUNSUPPORTED;
+  if (o->batched) return WAVE_EUNSUPPORTED;
+  (void)m;
+  return WAVE_OK;
+}
+
+extern "C" wave_status wave_gradient_workspace_size(wave_model m, const wave_shot* shots, int32_t nshots,
+                                                    const wave_gradient_opts* opts, size_t* bytes) {
+  if (!m || !bytes) return WAVE_EINVAL;
+  wave_status st = validate_shots(m, shots, nshots, false);
+  if (st != WAVE_OK) return st;
+  st = validate_opts(m, opts);
+  if (st != WAVE_OK) return st;
+  Carve c(nullptr);
+  GradWs w;
+  carve_gradient(c, m, shots, nshots, &w);
+  *bytes = c.off;
+  return WAVE_OK;
+}
+
+static double objective_weight(const wave_gradient_opts* o, const wave_shot& sh) {
+  if (o->objective == WAVE_OBJ_L2) return 1.0;
+  return sh.nrec > 0 ? 2.0 * o->patch_sign / sh.nrec : 0.0;
+}
+
+extern "C" wave_status wave_adjoint_sensitivity(wave_model m, const wave_shot* shots, int32_t nshots,
+                                                const wave_gradient_opts* opts, float* grad_dev,
+                                                double* misfit_dev, double* k_dev, void* ws, size_t ws_bytes,
+                                                void* stream) {
+  if (!m || !grad_dev) return WAVE_EINVAL;
+  wave_status st = validate_shots(m, shots, nshots, false);
+  if (st != WAVE_OK) return st;
+  st = validate_opts(m, opts);
+  if (st != WAVE_OK) return st;
+  if (opts->objective == WAVE_OBJ_PATCH && !(opts->patch_sign == 1.0 || opts->patch_sign == -1.0)) return WAVE_EINVAL;
+  size_t need = 0;
+  wave_gradient_workspace_size(m, shots, nshots, opts, &need);
+  if (!ws || ws_bytes < need || reinterpret_cast<uintptr_t>(ws) % 256) return WAVE_EWORKSPACE;
+  cudaStream_t s = (cudaStream_t)stream;
+  const Geom& g = m->g;
+  const int stor = m->d.storage;
+  const size_t eb = storage_bytes(stor);
+  const double dt = m->d.dt;
+  Carve c(ws);
+  GradWs w;
+  carve_gradient(c, m, shots, nshots, &w);
+  double* kd = w.scal + 0;
+  double* misfit_acc = misfit_dev ? misfit_dev : w.scal + 3;
+
+  CUDA_TRY(cudaMemsetAsync(w.acc, 0, g.cells * sizeof(float), s));
+  if (w.comp) CUDA_TRY(cudaMemsetAsync(w.comp, 0, g.cells * sizeof(float), s));
+  CUDA_TRY(cudaMemsetAsync(misfit_acc, 0, sizeof(double), s));
+  const bool auto_k = !(opts->k > 0.0);
+  if (!auto_k) CUDA_TRY(launch_set_k(kd, opts->k, s));
+  const double ratio = opts->k_ratio > 0.0 ? opts->k_ratio : 1e-2;
+
+  for (int si = 0; si < nshots; ++si) {
+    const wave_shot& sh = shots[si];
+    const int N = sh.nt;
+    const double wgt = objective_weight(opts, sh);
+    CUDA_TRY(launch_pitch_indices(g, sh.rec_cells_dev, sh.nrec, w.recp, s));
+    CUDA_TRY(cudaMemsetAsync(w.u0, 0, g.cells * eb, s));
+    CUDA_TRY(cudaMemsetAsync(w.u1, 0, g.cells * eb, s));
+    // levels 0 and 1 (Eq. IC), then inject f^1 into u^0
+    SparseArgs sp = sparse_args(m, w.recp, sh.nrec);
+    sp.observed = sh.observed_dev;
+    sp.obs_ld = N + 1;
+    sp.resid = w.resid;
+    sp.gsrc = w.u0;
+    sp.glevel = 0;
+    CUDA_TRY(launch_sparse(sp, stor, s));
+    sp.gsrc = w.u1;
+    sp.glevel = 1;
+    sp.dst = w.u0;
+    sp.src_p = pitched_cell(g, sh.src_cell);
+    sp.wavelet = sh.wavelet_dev;
+    sp.ilevel = 1;
+    CUDA_TRY(launch_sparse(sp, stor, s));
+    // ---- forward: propagate, adjoint source, -K(u,u) ------------------
+    void* prev = w.u0;
+    void* cur = w.u1;
+    for (int n = 1; n <= N; ++n) {
+      StepArgs a = step_args(m, cur, prev);
+      a.acc = w.acc;
+      a.comp = w.comp;
+      a.acc_scale = 1.f;
+      a.acc_mass = n <= N - 1;
+      a.acc_stiff = n <= N - 1;
+      CUDA_TRY(run_step(m, a, s));
+      std::swap(prev, cur);  // cur = u^{n+1}
+      if (n + 1 <= N) {
+        sp.gsrc = cur;
+        sp.glevel = n + 1;
+        sp.dst = prev;
+        sp.ilevel = n + 1;
+        CUDA_TRY(launch_sparse(sp, stor, s));
+      }
+    }
+    // ---- cost (Eq. cost1 / cost2) and k -------------------------------
+    const int64_t nres = (int64_t)(N + 1) * sh.nrec;
+    if (nres > 0) {
+      const int np = reduce_parts(nres);
+      CUDA_TRY(launch_sumsq_partial(w.resid, nullptr, nres, w.parts, np, s));
+      CUDA_TRY(launch_sum_final(w.parts, np, 0.5 * wgt * dt, 1, misfit_acc, s));
+    }
+    if (si == 0 && auto_k) {
+      const int np1 = reduce_parts(N);
+      CUDA_TRY(launch_sumsq_partial(sh.wavelet_dev + 1, nullptr, N, w.parts, np1, s));
+      CUDA_TRY(launch_sum_final(w.parts, np1, 1.0, 0, w.scal + 1, s));
+      const int64_t ne = (int64_t)N * sh.nrec;
+      if (ne > 0) {
+        const int np2 = reduce_parts(ne);
+        CUDA_TRY(launch_sumsq_partial(w.resid + sh.nrec, nullptr, ne, w.parts, np2, s));
+        CUDA_TRY(launch_sum_final(w.parts, np2, 1.0, 0, w.scal + 2, s));
+      } else {
+        CUDA_TRY(cudaMemsetAsync(w.scal + 2, 0, sizeof(double), s));
+      }
+      CUDA_TRY(launch_auto_k(w.scal + 1, w.scal + 2, ratio, wgt, kd, s));
+    }
+    // ---- superposed pass: u^s from (u^{N+1}, u^N), +K(u^s,u^s) ----------
+    // prev holds u^N, cur holds u^{N+1}
+    void* us_cur = prev;   // u^{s,j}
+    void* us_next = cur;   // u^{s,j+1}, overwritten with u^{s,j-1}
+    SparseArgs sb = sparse_args(m, w.recp, sh.nrec);
+    sb.src_p = pitched_cell(g, sh.src_cell);
+    sb.wavelet = sh.wavelet_dev;
+    sb.resid_in = w.resid;
+    sb.k_dev = kd;
+    sb.weight = (float)wgt;
+    for (int j = N; j >= 1; --j) {
+      sb.dst = us_next;
+      sb.ilevel = j;
+      CUDA_TRY(launch_sparse(sb, stor, s));
+      StepArgs a = step_args(m, us_cur, us_next);
+      a.acc = w.acc;
+      a.comp = w.comp;
+      a.acc_scale = -1.f;
+      a.acc_mass = 1;
+      a.acc_stiff = j <= N - 1;
+      CUDA_TRY(run_step(m, a, s));
+      std::swap(us_cur, us_next);  // us_cur = u^{s,j-1}, us_next = u^{s,j}
+    }
+  }
+  // ---- K~ = (K(u^s,u^s) - K(u,u)) / 2k (Eq. superposedkernel) ------------
+  CUDA_TRY(launch_finish(g, w.acc, kd, 1.0 / dt, 1, opts->grad_wrt == WAVE_GRAD_PARAM && m->d.physics == WAVE_VELOCITY,
+                         m->param, grad_dev, s));
+  if (k_dev) CUDA_TRY(cudaMemcpyAsync(k_dev, kd, sizeof(double), cudaMemcpyDeviceToDevice, s));
+  return WAVE_OK;
+}
+
+// ---------------------------------------------------------------------------
+// misfit
+// ---------------------------------------------------------------------------
+extern "C" size_t wave_misfit_scratch_size(int64_t count) {
+  return (size_t)reduce_parts(count < 1 ? 1 : count) * sizeof(double);
+}
+
+extern "C" wave_status misfit(const float* syn_dev, const float* obs_dev, int64_t count, double dt, double weight,
+                              double* out_dev, void* scratch_dev, size_t scratch_bytes, void* stream) {
+  if (!syn_dev || !out_dev || count < 0 || !(dt > 0)) return WAVE_EINVAL;
+  const int np = reduce_parts(count < 1 ? 1 : count);
+  if (!scratch_dev || scratch_bytes < (size_t)np * sizeof(double) ||
+      reinterpret_cast<uintptr_t>(scratch_dev) % 8)
+    return WAVE_EWORKSPACE;
+  cudaStream_t s = (cudaStream_t)stream;
+  double* parts = static_cast<double*>(scratch_dev);
+  CUDA_TRY(launch_sumsq_partial(syn_dev, obs_dev, count, parts, np, s));
+  CUDA_TRY(launch_sum_final(parts, np, 0.5 * weight * dt, 0, out_dev, s));
+  return WAVE_OK;
+}

@@ -1,0 +1,267 @@
+"""GPU (CUDA path through the C ABI) against the FP64 oracle.
+
+Bars: wavefields and traces within 1e-4 relative L2; the sensitivity K~
+within 1e-3 relative L2 at the same k; misfit within 1e-5.  The gap between
+K~ and the exact (stored-history) gradient is printed, not gated.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from _problems import make_problem, rel_l2
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+TRACE_TOL = 1e-4
+GRAD_TOL = 1e-3
+MISFIT_TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def W():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    import __graft_entry__ as g
+    g.build()
+    from paper_2509_15744_gb300 import wave
+    return wave
+
+
+DEV = "cuda"
+
+
+def gpu_shots(W, prob, with_observed=True):
+    shots = []
+    for i in range(len(prob.src)):
+        if prob.wavelets is not None:
+            wav = torch.from_numpy(prob.wavelets[i]).to(DEV)
+        else:
+            wav = W.wavelet(prob.wav_kind, prob.wav_freq, prob.dt, prob.nt[i], device=DEV)
+        obs = None
+        if with_observed and prob.observed is not None and prob.observed[i] is not None:
+            obs = torch.from_numpy(prob.observed[i]).to(DEV)
+        shots.append(W.Shot(prob.src[i], wav, torch.from_numpy(prob.rec[i]).to(DEV), obs))
+    return shots
+
+
+def gpu_model(W, prob, param=None, **kw):
+    p = prob.param0 if param is None else param
+    return W.Model(torch.from_numpy(np.ascontiguousarray(p)).to(DEV), prob.h, prob.dt, prob.order, prob.physics,
+                   prob.bc, **kw)
+
+
+# ---------------------------------------------------------------------------
+def test_wavelets(W):
+    dt, nt = 1e-3, 400
+    t = np.arange(nt + 1) * dt
+    r = W.wavelet("ricker", 15.0, dt, nt, device=DEV).cpu().numpy()
+    assert np.abs(r - O.ricker(t, 15.0)).max() < 1e-6
+    dt2 = 1.387e-6
+    s = W.wavelet("sine_burst", 10e3, dt2, 300, nc=2, psi0=1.0, device=DEV).cpu().numpy()
+    assert np.abs(s - O.sine_burst(np.arange(301) * dt2, 10e3, 2, 1.0)).max() < 1e-6
+
+
+FORWARD_CASES = [
+    # (shape, order, bc, physics, nt)
+    ((128, 128), 2, "dirichlet", "velocity", 400),
+    ((37, 45), 4, "neumann", "velocity", 120),
+    ((130, 261), 8, "dirichlet", "velocity", 150),
+    ((45, 140), 6, "neumann", "velocity", 120),
+    ((9, 9), 8, "dirichlet", "velocity", 40),
+    ((20, 21, 150), 8, "dirichlet", "velocity", 60),
+    ((17, 19, 23), 2, "neumann", "velocity", 60),
+    ((33, 12, 130), 4, "dirichlet", "velocity", 50),
+    ((11, 9, 9), 8, "neumann", "velocity", 30),
+    ((70, 140), 2, "neumann", "density", 200),
+    ((40, 37), 2, "dirichlet", "density", 150),
+]
+
+
+@pytest.mark.parametrize("shape,order,bc,physics,nt", FORWARD_CASES)
+def test_forward_traces_and_wavefields(W, shape, order, bc, physics, nt):
+    prob = make_problem(shape, order, bc, physics, nt=nt, nrec=40, seed=hash((shape, order)) % 1000,
+                        random_wavelet=True)
+    m = gpu_model(W, prob)
+    shots = gpu_shots(W, prob, with_observed=False)
+    traces, final = m.forward(shots, return_final=True)
+    torch.cuda.synchronize()
+    ref = O.forward(prob.medium(), prob.oracle_shots()[0], nt)
+    assert rel_l2(traces[0].cpu().numpy(), ref["traces"]) < TRACE_TOL
+    f = final.cpu().numpy()
+    assert rel_l2(f[0], ref["last"][0]) < TRACE_TOL
+    assert rel_l2(f[1], ref["last"][1]) < TRACE_TOL
+
+
+@pytest.mark.parametrize("shape,order,bc", [((33, 140), 8, "dirichlet"), ((29, 31), 4, "neumann"),
+                                            ((12, 14, 133), 6, "dirichlet")])
+def test_standing_mode_on_gpu(W, shape, order, bc):
+    # Closed-form discrete mode: u^n = cos(n w dt) phi (exact for the scheme).
+    h, v = 10.0, 2500.0
+    dt = O.cfl_dt(h, v, len(shape), order, 0.5)
+    grids = np.meshgrid(*[np.arange(n) for n in shape], indexing="ij")
+    phi = np.ones(shape)
+    mu = 0.0
+    c = O.stencil_weights(order)
+    for gi, n, k in zip(grids, shape, (2, 3, 1)[:len(shape)]):
+        th = np.pi * k / (n + 1) if bc == "dirichlet" else np.pi * k / n
+        phi = phi * (np.sin(th * (gi + 1)) if bc == "dirichlet" else np.cos(th * (gi + 0.5)))
+        mu += (c[0] + 2 * sum(c[j] * np.cos(j * th) for j in range(1, len(c)))) / h ** 2
+    cos_w = 1 + 0.5 * dt * dt * v * v * mu
+    nt = 200
+    m = W.Model(torch.full(shape, v, dtype=torch.float32, device=DEV), h, dt, order, "velocity", bc)
+    init = torch.from_numpy(np.stack([phi, cos_w * phi]).astype(np.float32)).to(DEV)
+    shot = W.Shot(0, torch.zeros(nt + 1, device=DEV), torch.arange(0, dtype=torch.int64, device=DEV))
+    _, final = m.forward([shot], init=init, return_final=True)
+    wdt = math.acos(cos_w)
+    assert rel_l2(final[0].cpu().numpy(), math.cos(nt * wdt) * phi) < 1e-4
+    assert rel_l2(final[1].cpu().numpy(), math.cos((nt + 1) * wdt) * phi) < 1e-4
+
+
+GRAD_CASES = [
+    # id, kwargs of make_problem, model kwargs
+    ("cfg0_full", dict(shape=(128, 128), order=2, bc="dirichlet", nt=400), {}),
+    ("o8_ragged", dict(shape=(50, 140), order=8, bc="dirichlet", nt=150, nrec=60), {}),
+    ("o6_neumann", dict(shape=(41, 77), order=6, bc="neumann", nt=120), {}),
+    ("o4_3d", dict(shape=(18, 20, 140), order=4, bc="dirichlet", nt=60, nrec=80), {}),
+    ("o8_3d", dict(shape=(16, 17, 19), order=8, bc="neumann", nt=50, nrec=30), {}),
+    ("kahan", dict(shape=(50, 140), order=8, bc="dirichlet", nt=150, nrec=60), {"kahan": True}),
+    ("two_shots", dict(shape=(45, 133), order=4, bc="dirichlet", nshots=2, nt_list=[90, 130], nrec=30), {}),
+    ("density_l2", dict(shape=(48, 150), physics="density", bc="dirichlet", nt=200, nrec=40), {}),
+]
+
+
+@pytest.mark.parametrize("case", GRAD_CASES, ids=[c[0] for c in GRAD_CASES])
+def test_gradient_matches_oracle(W, case):
+    _, kw, mkw = case
+    prob = make_problem(seed=5, **kw)
+    m = gpu_model(W, prob, **mkw)
+    grad, mis, kd = m.gradient(gpu_shots(W, prob))
+    torch.cuda.synchronize()
+    k = float(kd.item())
+    med = prob.medium()
+    shots = prob.oracle_shots()
+    ref = O.superposition_gradient(med, shots, max(prob.nt) if len(set(prob.nt)) == 1 else None, k) \
+        if len(set(prob.nt)) == 1 else None
+    if ref is None:  # uneven record lengths: sum the per-shot oracle results
+        kt = np.zeros(prob.shape)
+        c = 0.0
+        for s, n in zip(shots, prob.nt):
+            r = O.superposition_gradient(med, [s], n, k)
+            kt += r["K_tilde"]
+            c += r["C"]
+        ref = dict(K_tilde=kt, C=c)
+    g = grad.cpu().numpy()
+    err = rel_l2(g, ref["K_tilde"])
+    assert err < GRAD_TOL, err
+    assert abs(float(mis.item()) - ref["C"]) < MISFIT_TOL * abs(ref["C"])
+    # auto k follows the stated rule on the first shot
+    fw = O.forward(med, shots[0], prob.nt[0])
+    k_ref = O.auto_k(shots[0], O.adjoint_source(fw["traces"], shots[0], prob.nt[0]), prob.nt[0], 1e-2)
+    assert abs(k - k_ref) < 1e-4 * k_ref
+    if len(set(prob.nt)) == 1:
+        _, g_exact, _ = O.exact_gradient(med, shots, prob.nt[0])
+        print(f"\n{case[0]}: K~ vs oracle {err:.2e}; gap to exact gradient {rel_l2(g, g_exact):.2e}")
+
+
+def test_patch_objective_density(W):
+    shape = (60, 150)
+    ny, nx = shape
+    py, px = np.meshgrid(np.arange(20, 40), np.arange(120, 150), indexing="ij")
+    patch = (py * nx + px).ravel()
+    for sign in (1.0, -1.0):
+        prob = make_problem(shape, physics="density", bc="neumann", nt=220, objective="patch", patch=patch,
+                            src=ny // 2 * nx + 2, seed=3, patch_sign=sign)
+        m = gpu_model(W, prob)
+        grad, mis, kd = m.gradient(gpu_shots(W, prob, with_observed=False), objective="patch", patch_sign=sign)
+        torch.cuda.synchronize()
+        ref = O.superposition_gradient(prob.medium(), prob.oracle_shots(), prob.nt[0], float(kd.item()))
+        assert rel_l2(grad.cpu().numpy(), ref["K_tilde"]) < GRAD_TOL
+        assert abs(float(mis.item()) - ref["C"]) < MISFIT_TOL * abs(ref["C"])
+        assert math.copysign(1.0, float(mis.item())) == sign
+
+
+def test_explicit_k_and_grad_wrt_param(W):
+    prob = make_problem((40, 130), order=4, nt=100, seed=8)
+    m = gpu_model(W, prob)
+    k = 3.7
+    grad_m, _, kd = m.gradient(gpu_shots(W, prob), k=k)
+    grad_v, _, _ = m.gradient(gpu_shots(W, prob), k=k, grad_wrt="param")
+    torch.cuda.synchronize()
+    assert float(kd.item()) == k
+    ref = O.superposition_gradient(prob.medium(), prob.oracle_shots(), prob.nt[0], k)
+    assert rel_l2(grad_m.cpu().numpy(), ref["K_tilde"]) < GRAD_TOL
+    ref_v = prob.medium().param_chain(ref["K_tilde"])
+    assert rel_l2(grad_v.cpu().numpy(), ref_v) < GRAD_TOL
+
+
+def test_misfit_entry_point(W):
+    rng = np.random.default_rng(1)
+    a = rng.standard_normal(1_000_003).astype(np.float32)
+    b = rng.standard_normal(1_000_003).astype(np.float32)
+    out = W.misfit(torch.from_numpy(a).to(DEV), torch.from_numpy(b).to(DEV), 0.25, 1.0)
+    ref = O.misfit(a.astype(np.float64), b.astype(np.float64), 0.25)
+    assert abs(float(out.item()) - ref) < 1e-12 * ref
+    out0 = W.misfit(torch.from_numpy(a).to(DEV), None, 0.5, 2.0)
+    assert abs(float(out0.item()) - O.misfit(a.astype(np.float64), None, 0.5, 2.0)) < 1e-12 * float(out0.item())
+    empty = W.misfit(torch.zeros(0, device=DEV), None, 0.5)
+    assert float(empty.item()) == 0.0
+
+
+# ---------------------------------------------------------------------------
+# edge cases
+# ---------------------------------------------------------------------------
+def test_receivers_duplicated_at_source_and_out_of_range(W):
+    shape = (30, 131)
+    prob = make_problem(shape, order=4, nt=80, seed=12)
+    src = prob.src[0]
+    rec = np.array([src, src, 5, 5, 17 * 131 + 130, 0], np.int64)
+    prob.rec = [rec]
+    tr = O.forward(prob.medium(prob.param_true), O.Shot(src, prob.oracle_wavelet(0), rec), 80)["traces"]
+    prob.observed = [tr.astype(np.float32)]
+    m = gpu_model(W, prob)
+    grad, mis, kd = m.gradient(gpu_shots(W, prob))
+    torch.cuda.synchronize()
+    ref = O.superposition_gradient(prob.medium(), prob.oracle_shots(), 80, float(kd.item()))
+    assert rel_l2(grad.cpu().numpy(), ref["K_tilde"]) < GRAD_TOL
+    # an out-of-range receiver gives a zero trace and changes nothing else
+    bad = torch.tensor([3, -1, 10 ** 9, 7], dtype=torch.int64, device=DEV)
+    wav = W.wavelet("ricker", prob.wav_freq, prob.dt, 80, device=DEV)
+    traces = m.forward([W.Shot(src, wav, bad)])[0].cpu().numpy()
+    good = m.forward([W.Shot(src, wav, torch.tensor([3, 7], dtype=torch.int64, device=DEV))])[0].cpu().numpy()
+    assert np.all(traces[1] == 0) and np.all(traces[2] == 0)
+    assert np.array_equal(traces[[0, 3]], good)
+
+
+def test_no_receivers_and_single_step(W):
+    prob = make_problem((20, 40), order=2, nt=1, seed=2)
+    m = gpu_model(W, prob)
+    wav = W.wavelet("ricker", prob.wav_freq, prob.dt, 1, device=DEV)
+    shot = W.Shot(prob.src[0], wav, torch.zeros(0, dtype=torch.int64, device=DEV))
+    grad, mis, kd = m.gradient([shot])
+    torch.cuda.synchronize()
+    assert float(mis.item()) == 0.0 and float(kd.item()) == 1.0
+    assert torch.isfinite(grad).all()
+    # N = 1: no half level below N+1/2 enters either sum, so K~ is exactly zero
+    assert float(grad.abs().max().item()) == 0.0
+
+
+def test_unstable_time_step_is_rejected(W):
+    v = torch.full((32, 32), 3000.0, device=DEV)
+    dt = O.cfl_dt(10.0, 3000.0, 2, 8, 1.01)
+    with pytest.raises(W.WaveError) as e:
+        W.Model(v, 10.0, dt, 8)
+    assert e.value.status == 2
+    W.Model(v, 10.0, O.cfl_dt(10.0, 3000.0, 2, 8, 0.99), 8)
+
+
+def test_kernels_run_through_the_library(W):
+    before = W.launch_count()
+    prob = make_problem((20, 40), order=2, nt=10, seed=2)
+    m = gpu_model(W, prob)
+    m.gradient(gpu_shots(W, prob))
+    torch.cuda.synchronize()
+    assert W.launch_count() - before >= 4 * 10
