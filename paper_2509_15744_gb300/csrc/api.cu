@@ -633,7 +633,8 @@ extern "C" size_t wave_misfit_scratch_size(int64_t count) {
 
 extern "C" wave_status misfit(const float* syn_dev, const float* obs_dev, int64_t count, double dt, double weight,
                               double* out_dev, void* scratch_dev, size_t scratch_bytes, void* stream) {
-  if (!syn_dev || !out_dev || count < 0 || !(dt > 0)) return WAVE_EINVAL;
+  if (!out_dev || count < 0 || !(dt > 0)) return WAVE_EINVAL;
+  if (count > 0 && !syn_dev) return WAVE_EINVAL;
   const int np = reduce_parts(count < 1 ? 1 : count);
   if (!scratch_dev || scratch_bytes < (size_t)np * sizeof(double) ||
       reinterpret_cast<uintptr_t>(scratch_dev) % 8)

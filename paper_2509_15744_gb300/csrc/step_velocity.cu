@@ -75,12 +75,15 @@ __device__ __forceinline__ void stage_x_halo(float* srow, const T* __restrict__ 
 }
 
 // x part of the stencil for the 4 cells of a lane: positions 4+4l+i in srow.
+// The lane's own float4 is read back from the staged row, not taken from the
+// register queue: when the row ends inside it (nx not a multiple of 4), its
+// cells beyond nx hold the mirrored ghost values written by stage_x_halo.
 template <int R>
-__device__ __forceinline__ void x_terms(const float* srow, const float4& own, int lane, float lap[4],
-                                        float ndim_c0) {
+__device__ __forceinline__ void x_terms(const float* srow, int lane, float lap[4], float ndim_c0) {
   const float4 A = *reinterpret_cast<const float4*>(srow + 4 * lane);
+  const float4 B = *reinterpret_cast<const float4*>(srow + 4 + 4 * lane);
   const float4 C = *reinterpret_cast<const float4*>(srow + 8 + 4 * lane);
-  const float e[12] = {A.x, A.y, A.z, A.w, own.x, own.y, own.z, own.w, C.x, C.y, C.z, C.w};
+  const float e[12] = {A.x, A.y, A.z, A.w, B.x, B.y, B.z, B.w, C.x, C.y, C.z, C.w};
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
     float s = ndim_c0 * e[4 + i];
@@ -178,7 +181,7 @@ step2d_velocity_kernel(StepArgs a) {
     stage_x_halo<R, T>(srow, uc, y * g.px, x0, xin, lane, g);
     __syncwarp();
     float lap[4];
-    x_terms<R>(srow, q[R], lane, lap, 2.f * cw<R>(0));
+    x_terms<R>(srow, lane, lap, 2.f * cw<R>(0));
 #pragma unroll
     for (int j = 1; j <= R; ++j) {
       lap[0] = fmaf(cw<R>(j), q[R - j].x + q[R + j].x, lap[0]);
@@ -268,7 +271,7 @@ step3d_velocity_kernel(StepArgs a) {
     __syncthreads();
     if (row_valid) {
       float lap[4];
-      x_terms<R>(srow, q[R], lane, lap, 3.f * cw<R>(0));
+      x_terms<R>(srow, lane, lap, 3.f * cw<R>(0));
 #pragma unroll
       for (int j = 1; j <= R; ++j) {
         const float4 ym = *reinterpret_cast<const float4*>(&sm[buf][R + warp - j][4 + 4 * lane]);

@@ -96,6 +96,46 @@ def test_forward_traces_and_wavefields(W, shape, order, bc, physics, nt):
     assert rel_l2(f[1], ref["last"][1]) < TRACE_TOL
 
 
+ONE_STEP_SHAPES = [(37, 45), (9, 130), (21, 259), (40, 131), (13, 9), (10, 11, 133), (19, 9, 10), (12, 17, 258)]
+
+
+@pytest.mark.parametrize("bc", ["dirichlet", "neumann"])
+@pytest.mark.parametrize("order", [2, 4, 6, 8])
+@pytest.mark.parametrize("shape", ONE_STEP_SHAPES)
+def test_one_step_from_random_levels(W, shape, order, bc):
+    # One leapfrog step from random u^0, u^1 checks every cell of every
+    # ragged tile edge (x not a multiple of 4 or 128, y not a multiple of 8).
+    if min(shape) < order + 1:
+        pytest.skip("grid smaller than the stencil")
+    rng = np.random.default_rng(len(shape) * 100 + order)
+    v = rng.uniform(2000, 3000, shape).astype(np.float32)
+    dt = O.cfl_dt(10.0, 3000.0, len(shape), order, 0.5)
+    lv = rng.standard_normal((2,) + shape).astype(np.float32)
+    m = W.Model(torch.from_numpy(v).to(DEV), 10.0, dt, order, "velocity", bc)
+    shot = W.Shot(0, torch.zeros(2, device=DEV), torch.zeros(0, dtype=torch.int64, device=DEV))
+    _, fin = m.forward([shot], init=torch.from_numpy(lv).to(DEV), return_final=True)
+    ref = O.Medium("velocity", v.astype(np.float64), 10.0, dt, order, bc).step(
+        lv[0].astype(np.float64), lv[1].astype(np.float64), np.zeros(shape))
+    got = fin[1].cpu().numpy()
+    assert np.abs(got - ref).max() < 1e-5 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("bc", ["dirichlet", "neumann"])
+@pytest.mark.parametrize("shape", [(37, 45), (21, 259), (9, 130)])
+def test_one_step_density_from_random_levels(W, shape, bc):
+    rng = np.random.default_rng(7)
+    gam = rng.uniform(0.1, 1.0, shape).astype(np.float32)
+    h = 2e-3
+    dt = O.cfl_dt(h, 509.8366, 2, 2, 0.5)
+    lv = rng.standard_normal((2,) + shape).astype(np.float32)
+    m = W.Model(torch.from_numpy(gam).to(DEV), h, dt, 2, "density", bc)
+    shot = W.Shot(0, torch.zeros(2, device=DEV), torch.zeros(0, dtype=torch.int64, device=DEV))
+    _, fin = m.forward([shot], init=torch.from_numpy(lv).to(DEV), return_final=True)
+    ref = O.Medium("density", gam.astype(np.float64), h, dt, 2, bc).step(
+        lv[0].astype(np.float64), lv[1].astype(np.float64), np.zeros(shape))
+    assert np.abs(fin[1].cpu().numpy() - ref).max() < 1e-5 * np.abs(ref).max()
+
+
 @pytest.mark.parametrize("shape,order,bc", [((33, 140), 8, "dirichlet"), ((29, 31), 4, "neumann"),
                                             ((12, 14, 133), 6, "dirichlet")])
 def test_standing_mode_on_gpu(W, shape, order, bc):
@@ -106,7 +146,10 @@ def test_standing_mode_on_gpu(W, shape, order, bc):
     phi = np.ones(shape)
     mu = 0.0
     c = O.stencil_weights(order)
-    for gi, n, k in zip(grids, shape, (2, 3, 1)[:len(shape)]):
+    # mid-band modes (theta near pi/2): a very smooth mode would measure the
+    # FP32 cancellation inside the Laplacian rather than the scheme
+    for gi, n in zip(grids, shape):
+        k = n // 2
         th = np.pi * k / (n + 1) if bc == "dirichlet" else np.pi * k / n
         phi = phi * (np.sin(th * (gi + 1)) if bc == "dirichlet" else np.cos(th * (gi + 0.5)))
         mu += (c[0] + 2 * sum(c[j] * np.cos(j * th) for j in range(1, len(c)))) / h ** 2
@@ -173,15 +216,22 @@ def test_patch_objective_density(W):
     py, px = np.meshgrid(np.arange(20, 40), np.arange(120, 150), indexing="ij")
     patch = (py * nx + px).ravel()
     for sign in (1.0, -1.0):
-        prob = make_problem(shape, physics="density", bc="neumann", nt=220, objective="patch", patch=patch,
-                            src=ny // 2 * nx + 2, seed=3, patch_sign=sign)
+        prob = make_problem(shape, physics="density", bc="neumann", nt=300, objective="patch", patch=patch,
+                            src=ny // 2 * nx + 60, seed=3, patch_sign=sign)
         m = gpu_model(W, prob)
-        grad, mis, kd = m.gradient(gpu_shots(W, prob, with_observed=False), objective="patch", patch_sign=sign)
+        # The patch adjoint field is concentrated near the patch, so k u_adj / u
+        # is locally much smaller than the global ratio near the source; a
+        # larger ratio keeps the FP32 cancellation of Eq. superposedkernel
+        # below the parity bar there (Sec. 4.1: too small a k shows up as
+        # FP32/FP64 disagreement).
+        grad, mis, kd = m.gradient(gpu_shots(W, prob, with_observed=False), objective="patch", patch_sign=sign,
+                                   k_ratio=5e-2)
         torch.cuda.synchronize()
         ref = O.superposition_gradient(prob.medium(), prob.oracle_shots(), prob.nt[0], float(kd.item()))
         assert rel_l2(grad.cpu().numpy(), ref["K_tilde"]) < GRAD_TOL
         assert abs(float(mis.item()) - ref["C"]) < MISFIT_TOL * abs(ref["C"])
         assert math.copysign(1.0, float(mis.item())) == sign
+        assert abs(ref["C"]) > 0 and np.abs(ref["K_tilde"]).max() > 0
 
 
 def test_explicit_k_and_grad_wrt_param(W):
