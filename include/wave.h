@@ -211,6 +211,22 @@ wave_status misfit(const float* syn_dev, const float* obs_dev, int64_t count, do
                    double weight, double* out_dev, void* scratch_dev, size_t scratch_bytes,
                    void* stream);
 
+/* ---- misfit without caller scratch ----------------------------------------
+ * The paper has no counterpart: this is a library convenience.  Same result as
+ * misfit() (FP64, within rounding of the summation order) for callers that
+ * cannot allocate device memory -- e.g. a plugin whose host framework has
+ * reserved all device memory for its own allocator, or a latency-critical loop
+ * that must not enter an allocator.  The partial sums live in a static device
+ * array inside the library (32 KB per GPU that loads it, held until exit), so
+ * count is limited to 33,554,432 samples; larger counts return WAVE_EINVAL
+ * before any work is enqueued.  Allocates nothing.  All calls on a GPU share
+ * the array: calls whose kernels may overlap on the GPU (e.g. on unordered
+ * streams) race and must not be issued.  The first call on a device looks up
+ * the array's address (cudaGetSymbolAddress, with that device current); make
+ * it before any stream capture starts. */
+wave_status wave_misfit_static(const float* syn_dev, const float* obs_dev, int64_t count, double dt,
+                               double weight, double* out_dev, void* stream);
+
 #ifdef __cplusplus
 }
 #endif
