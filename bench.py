@@ -44,13 +44,37 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain-path comparison")
+    # reduced sizes, for profiling captures only (the line is marked "reduced")
+    ap.add_argument("--shape", default=None, help="override the grid shape, e.g. 256,256,256")
+    ap.add_argument("--shots", type=int, default=None, help="use the first K shots")
+    ap.add_argument("--nt", type=int, default=None, help="override every record length")
     return ap.parse_args()
 
 
-def make_workload(name):
+def make_workload(name, shape=None, shots=None, nt=None):
     from paper_2509_15744_gb300 import workloads as WL
-    return {"w0": WL.workload0, "w1": WL.workload1, "w2": WL.workload2, "w3": WL.workload3,
-            "w4": WL.workload4}[name]()
+    if shape is not None:
+        shape = tuple(int(v) for v in shape.split(","))
+        if name == "w2":
+            wl = WL.workload2(shape=shape)
+        elif name == "w0":
+            wl = WL.workload0(n=shape[0])
+        elif name == "w1":
+            wl = WL.workload1(n=shape[0])
+        elif name == "w3":
+            wl = WL.workload3(n=shape[0])
+        else:
+            wl = WL.workload4(n=shape[0])
+    else:
+        wl = {"w0": WL.workload0, "w1": WL.workload1, "w2": WL.workload2, "w3": WL.workload3,
+              "w4": WL.workload4}[name]()
+    if shots is not None:
+        wl.sources, wl.receivers, wl.nt = wl.sources[:shots], wl.receivers[:shots], wl.nt[:shots]
+    if nt is not None:
+        wl.nt = [int(nt)] * len(wl.nt)
+    if shape is not None or shots is not None or nt is not None:
+        wl.name += "_reduced"
+    return wl
 
 
 def units_of(wl):
@@ -88,7 +112,7 @@ def oracle_sample(wl, crop=160, nt=2):
 def run_reference(args, rank, world):
     if rank != 0:
         return
-    wl = make_workload(args.workload)
+    wl = make_workload(args.workload, args.shape, args.shots, args.nt)
     crop = 192 if wl.ndim == 3 else 2048
     rates = []
     desc = ""
@@ -217,7 +241,7 @@ def main():
     ge.build()
     from paper_2509_15744_gb300 import wave as W
 
-    wl = make_workload(args.workload)
+    wl = make_workload(args.workload, args.shape, args.shots, args.nt)
     dt = W.cfl_dt(wl.ndim, wl.order, wl.h, wl.vmax, wl.cfl_fraction)
     mode = "plain" if args.mode in ("auto", "plain") else "batched"
 
