@@ -172,6 +172,10 @@ wave_status wave_model_destroy(wave_model model);
  * >= 1 is valid; it changes speed, never results. */
 wave_status wave_model_set_block(wave_model model, int64_t zblock);
 wave_status wave_model_get_block(wave_model model, int64_t* zblock);
+/* Full tiling of the 3D FP32 step kernel: zblock as above, tile_rows (8 or 16
+ * rows of 128 cells per CTA) and ring_depth (2 or 3 planes staged ahead in
+ * the shared-memory ring).  Speed only; results are identical. */
+wave_status wave_model_set_tiling(wave_model model, int64_t zblock, int32_t tile_rows, int32_t ring_depth);
 
 /* ---- forward ---------------------------------------------------------------
  * Leapfrog u^{n+1} = 2u^n - u^{n-1} + dt^2/a (L u^n + f^n) for n = 1..N_s with

@@ -74,6 +74,8 @@ struct wave_model_s {
   float* coef;
   float* bmat;
   int64_t zblock;
+  int tile_rows;     // 3D ring kernel: 8 or 16 rows per CTA
+  int ring_depth;    // 3D ring kernel: 2 or 3 planes copied ahead
   double stability;
 };
 
@@ -210,6 +212,8 @@ wave_status wave_model_create(const wave_grid_desc* desc, const float* param_dev
   m->coef = coef;
   m->bmat = bmat;
   m->zblock = default_zblock(g);
+  m->tile_rows = 8;
+  m->ring_depth = 3;
   m->stability = host_max;
   *out = m;
   return WAVE_OK;
@@ -230,6 +234,16 @@ wave_status wave_model_set_block(wave_model model, int64_t zblock) {
 wave_status wave_model_get_block(wave_model model, int64_t* zblock) {
   if (!model || !zblock) return WAVE_EINVAL;
   *zblock = model->zblock;
+  return WAVE_OK;
+}
+
+wave_status wave_model_set_tiling(wave_model model, int64_t zblock, int32_t tile_rows, int32_t ring_depth) {
+  if (!model || zblock < 1) return WAVE_EINVAL;
+  if (tile_rows != 8 && tile_rows != 16) return WAVE_EINVAL;
+  if (ring_depth != 2 && ring_depth != 3) return WAVE_EINVAL;
+  model->zblock = zblock;
+  model->tile_rows = tile_rows;
+  model->ring_depth = ring_depth;
   return WAVE_OK;
 }
 
@@ -265,6 +279,8 @@ static StepArgs step_args(const wave_model_s* m, const void* cur, void* prev) {
   a.da = m->d.physics == WAVE_DENSITY ? (float)kDa : 1.f;
   a.dbs = m->d.physics == WAVE_DENSITY ? (float)(m->d.dt * m->d.dt / (m->d.h * m->d.h) * kDb) : 0.f;
   a.zblock = m->zblock;
+  a.tile_rows = m->tile_rows;
+  a.ring_depth = m->ring_depth;
   return a;
 }
 

@@ -131,11 +131,14 @@ struct StepArgs {
   float da;              // d a / d gamma (density); 1 for velocity
   float dbs;             // (dt^2/h^2) d b / d gamma (density)
   int64_t zblock;        // cells of the march axis per CTA (3D) / warp (2D)
+  int tile_rows;         // 3D ring kernel: rows per CTA (8 or 16)
+  int ring_depth;        // 3D ring kernel: planes copied ahead (2 or 3)
 };
 
 // Launchers (defined in step_*.cu).  Return cudaGetLastError() of the launch.
 cudaError_t launch_step_velocity(const StepArgs& a, int order, int storage, cudaStream_t s);
 cudaError_t launch_step_density(const StepArgs& a, int storage, cudaStream_t s);
+cudaError_t launch_step3d_ring(const StepArgs& a, int order, cudaStream_t s);
 
 // ---- sparse (source / receiver) kernel -----------------------------------
 struct SparseArgs {

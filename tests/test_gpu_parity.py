@@ -120,6 +120,23 @@ def test_one_step_from_random_levels(W, shape, order, bc):
     assert np.abs(got - ref).max() < 1e-5 * np.abs(ref).max()
 
 
+@pytest.mark.parametrize("order", [2, 8])
+def test_3d_tilings_give_identical_results(W, order):
+    # Every tiling of the 3D step kernel performs the same arithmetic per cell.
+    shape = (37, 27, 261)
+    prob = make_problem(shape, order, "dirichlet", nt=12, nrec=50, seed=4, random_wavelet=True)
+    m = gpu_model(W, prob)
+    shots = gpu_shots(W, prob, with_observed=False)
+    base_tr, base_fin = m.forward(shots, return_final=True)
+    g0, _, _ = m.gradient(gpu_shots(W, prob), k=2.0)
+    for zb, rows, depth in [(64, 8, 2), (64, 16, 3), (7, 16, 2), (5, 8, 3), (37, 16, 3), (1, 8, 2)]:
+        m.set_tiling(zb, rows, depth)
+        tr, fin = m.forward(shots, return_final=True)
+        g1, _, _ = m.gradient(gpu_shots(W, prob), k=2.0)
+        assert torch.equal(tr[0], base_tr[0]) and torch.equal(fin, base_fin), (zb, rows, depth)
+        assert torch.equal(g1, g0), (zb, rows, depth)
+
+
 @pytest.mark.parametrize("bc", ["dirichlet", "neumann"])
 @pytest.mark.parametrize("shape", [(37, 45), (21, 259), (9, 130)])
 def test_one_step_density_from_random_levels(W, shape, bc):
