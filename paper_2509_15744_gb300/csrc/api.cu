@@ -328,6 +328,34 @@ static cudaError_t run_step(const wave_model_s* m, const StepArgs& a, cudaStream
   return err;
 }
 
+static cudaError_t run_batched(const wave_model_s* m, const BatchArgs& b, cudaStream_t s) {
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (g_timing.on) {
+    while (g_timing.ev.size() < g_timing.used + 2) {
+      cudaEvent_t e;
+      cudaError_t err = cudaEventCreate(&e);
+      if (err != cudaSuccess) return err;
+      g_timing.ev.push_back(e);
+    }
+    e0 = g_timing.ev[g_timing.used];
+    e1 = g_timing.ev[g_timing.used + 1];
+    g_timing.used += 2;
+    cudaEventRecord(e0, s);
+  }
+  cudaError_t err = launch_step3d_batched(b, m->d.order, s);
+  if (g_timing.on) {
+    cudaEventRecord(e1, s);
+    const double cells = (double)(m->g.nx * m->g.ny * m->g.nz);
+    bool any = false;
+    for (int i = 0; i < b.nshots; ++i) any |= b.accf[i] != 0;
+    // per shot: read u^n, u^{n-1}, write u^{n+1}; once: coef, acc (+comp) RMW
+    double per_cell = 12.0 * b.nshots + 4.0 + (any ? (b.base.comp ? 16.0 : 8.0) : 0.0);
+    g_timing.bytes += cells * per_cell;
+    g_timing.launches += 1;
+  }
+  return err;
+}
+
 extern "C" wave_status wave_timing_enable(int32_t on) {
   g_timing.on = on != 0;
   g_timing.used = 0;
@@ -491,9 +519,42 @@ static wave_status validate_opts(const wave_model_s* m, const wave_gradient_opts
   if (o->mode != WAVE_SUPERPOSITION && o->mode != WAVE_EXACT_STORED) return WAVE_EINVAL;
   if (o->grad_wrt != WAVE_GRAD_MASS && o->grad_wrt != WAVE_GRAD_PARAM) return WAVE_EINVAL;
   if (o->mode == WAVE_EXACT_STORED) return WAVE_EUNSUPPORTED;
-  if (o->batched) return WAVE_EUNSUPPORTED;
-  (void)m;
+  if (o->batched && !(m->d.ndim == 3 && m->d.physics == WAVE_VELOCITY && m->d.storage == WAVE_F32))
+    return WAVE_EUNSUPPORTED;
   return WAVE_OK;
+}
+
+static double objective_weight(const wave_gradient_opts* o, const wave_shot& sh) {
+  if (o->objective == WAVE_OBJ_L2) return 1.0;
+  return sh.nrec > 0 ? 2.0 * o->patch_sign / sh.nrec : 0.0;
+}
+
+// Batched mode keeps every shot's two levels and residual traces resident.
+struct BatchWs {
+  float* acc;
+  float* comp;
+  std::vector<void*> u0, u1;
+  std::vector<float*> resid;
+  std::vector<int64_t*> recp;
+  double* parts;
+  double* scal;
+};
+
+static void carve_batched(Carve& c, const wave_model_s* m, const wave_shot* shots, int32_t nshots, BatchWs* w) {
+  w->acc = c.take<float>(m->g.cells);
+  w->comp = m->d.kahan ? c.take<float>(m->g.cells) : nullptr;
+  w->u0.resize(nshots);
+  w->u1.resize(nshots);
+  w->resid.resize(nshots);
+  w->recp.resize(nshots);
+  for (int s = 0; s < nshots; ++s) {
+    w->u0[s] = c.take<float>(m->g.cells);
+    w->u1[s] = c.take<float>(m->g.cells);
+    w->resid[s] = c.take<float>(std::max<int64_t>(1, (int64_t)(shots[s].nt + 1) * shots[s].nrec));
+    w->recp[s] = c.take<int64_t>(std::max(1, shots[s].nrec));
+  }
+  w->parts = c.take<double>(1024);
+  w->scal = c.take<double>(4);
 }
 
 extern "C" wave_status wave_gradient_workspace_size(wave_model m, const wave_shot* shots, int32_t nshots,
@@ -504,16 +565,164 @@ extern "C" wave_status wave_gradient_workspace_size(wave_model m, const wave_sho
   st = validate_opts(m, opts);
   if (st != WAVE_OK) return st;
   Carve c(nullptr);
-  GradWs w;
-  carve_gradient(c, m, shots, nshots, &w);
+  if (opts->batched) {
+    BatchWs w;
+    carve_batched(c, m, shots, nshots, &w);
+  } else {
+    GradWs w;
+    carve_gradient(c, m, shots, nshots, &w);
+  }
   *bytes = c.off;
   return WAVE_OK;
 }
 
-static double objective_weight(const wave_gradient_opts* o, const wave_shot& sh) {
-  if (o->objective == WAVE_OBJ_L2) return 1.0;
-  return sh.nrec > 0 ? 2.0 * o->patch_sign / sh.nrec : 0.0;
+static wave_status gradient_batched(wave_model m, const wave_shot* shots, int32_t nshots,
+                                    const wave_gradient_opts* opts, float* grad_dev, double* misfit_dev,
+                                    double* k_dev, void* ws, cudaStream_t s) {
+  const Geom& g = m->g;
+  const double dt = m->d.dt;
+  Carve c(ws);
+  BatchWs w;
+  carve_batched(c, m, shots, nshots, &w);
+  double* kd = w.scal + 0;
+  double* misfit_acc = misfit_dev ? misfit_dev : w.scal + 3;
+  CUDA_TRY(cudaMemsetAsync(w.acc, 0, g.cells * sizeof(float), s));
+  if (w.comp) CUDA_TRY(cudaMemsetAsync(w.comp, 0, g.cells * sizeof(float), s));
+  CUDA_TRY(cudaMemsetAsync(misfit_acc, 0, sizeof(double), s));
+  const bool auto_k = !(opts->k > 0.0);
+  if (!auto_k) CUDA_TRY(launch_set_k(kd, opts->k, s));
+  const double ratio = opts->k_ratio > 0.0 ? opts->k_ratio : 1e-2;
+  std::vector<void*> prev(nshots), cur(nshots);
+  std::vector<SparseArgs> sp(nshots);
+  int nmax = 0;
+  for (int si = 0; si < nshots; ++si) {
+    const wave_shot& sh = shots[si];
+    nmax = std::max(nmax, sh.nt);
+    CUDA_TRY(launch_pitch_indices(g, sh.rec_cells_dev, sh.nrec, w.recp[si], s));
+    CUDA_TRY(cudaMemsetAsync(w.u0[si], 0, g.cells * sizeof(float), s));
+    CUDA_TRY(cudaMemsetAsync(w.u1[si], 0, g.cells * sizeof(float), s));
+    SparseArgs a = sparse_args(m, w.recp[si], sh.nrec);
+    a.observed = sh.observed_dev;
+    a.obs_ld = sh.nt + 1;
+    a.resid = w.resid[si];
+    a.gsrc = w.u0[si];
+    a.glevel = 0;
+    CUDA_TRY(launch_sparse(a, WAVE_F32, s));
+    a.gsrc = w.u1[si];
+    a.glevel = 1;
+    a.dst = w.u0[si];
+    a.src_p = pitched_cell(g, sh.src_cell);
+    a.wavelet = sh.wavelet_dev;
+    a.ilevel = 1;
+    CUDA_TRY(launch_sparse(a, WAVE_F32, s));
+    sp[si] = a;
+    prev[si] = w.u0[si];
+    cur[si] = w.u1[si];
+  }
+  StepArgs base = step_args(m, nullptr, nullptr);
+  base.acc = w.acc;
+  base.comp = w.comp;
+  // ---- forward: all shots start at t = 0 --------------------------------
+  for (int n = 1; n <= nmax; ++n) {
+    BatchArgs b;
+    memset(&b, 0, sizeof(b));
+    b.base = base;
+    b.base.acc_scale = 1.f;
+    for (int si = 0; si < nshots; ++si) {
+      if (shots[si].nt < n) continue;
+      b.cur[b.nshots] = static_cast<const float*>(cur[si]);
+      b.prev[b.nshots] = static_cast<float*>(prev[si]);
+      b.accf[b.nshots] = n <= shots[si].nt - 1;
+      if (++b.nshots == kMaxBatch) {
+        CUDA_TRY(run_batched(m, b, s));
+        b.nshots = 0;
+      }
+    }
+    if (b.nshots) CUDA_TRY(run_batched(m, b, s));
+    for (int si = 0; si < nshots; ++si) {
+      if (shots[si].nt < n) continue;
+      std::swap(prev[si], cur[si]);
+      if (n + 1 <= shots[si].nt) {
+        sp[si].gsrc = cur[si];
+        sp[si].glevel = n + 1;
+        sp[si].dst = prev[si];
+        sp[si].ilevel = n + 1;
+        CUDA_TRY(launch_sparse(sp[si], WAVE_F32, s));
+      }
+    }
+  }
+  // ---- cost and k -----------------------------------------------------------
+  for (int si = 0; si < nshots; ++si) {
+    const wave_shot& sh = shots[si];
+    const double wgt = objective_weight(opts, sh);
+    const int64_t nres = (int64_t)(sh.nt + 1) * sh.nrec;
+    if (nres > 0) {
+      const int np = reduce_parts(nres);
+      CUDA_TRY(launch_sumsq_partial(w.resid[si], nullptr, nres, w.parts, np, s));
+      CUDA_TRY(launch_sum_final(w.parts, np, 0.5 * wgt * dt, 1, misfit_acc, s));
+    }
+  }
+  if (auto_k) {
+    const wave_shot& sh = shots[0];
+    const int N = sh.nt;
+    const int np1 = reduce_parts(N);
+    CUDA_TRY(launch_sumsq_partial(sh.wavelet_dev + 1, nullptr, N, w.parts, np1, s));
+    CUDA_TRY(launch_sum_final(w.parts, np1, 1.0, 0, w.scal + 1, s));
+    const int64_t ne = (int64_t)N * sh.nrec;
+    if (ne > 0) {
+      const int np2 = reduce_parts(ne);
+      CUDA_TRY(launch_sumsq_partial(w.resid[0] + sh.nrec, nullptr, ne, w.parts, np2, s));
+      CUDA_TRY(launch_sum_final(w.parts, np2, 1.0, 0, w.scal + 2, s));
+    } else {
+      CUDA_TRY(cudaMemsetAsync(w.scal + 2, 0, sizeof(double), s));
+    }
+    CUDA_TRY(launch_auto_k(w.scal + 1, w.scal + 2, ratio, objective_weight(opts, sh), kd, s));
+  }
+  // ---- superposed pass: shot s runs j = N_s..1 at global steps t = j --------
+  std::vector<void*> us_cur(nshots), us_next(nshots);
+  std::vector<SparseArgs> sb(nshots);
+  for (int si = 0; si < nshots; ++si) {
+    us_cur[si] = prev[si];   // u^{N}
+    us_next[si] = cur[si];   // u^{N+1}
+    sb[si] = sparse_args(m, w.recp[si], shots[si].nrec);
+    sb[si].src_p = pitched_cell(g, shots[si].src_cell);
+    sb[si].wavelet = shots[si].wavelet_dev;
+    sb[si].resid_in = w.resid[si];
+    sb[si].k_dev = kd;
+    sb[si].weight = (float)objective_weight(opts, shots[si]);
+  }
+  for (int t = nmax; t >= 1; --t) {
+    for (int si = 0; si < nshots; ++si) {
+      if (shots[si].nt < t) continue;
+      sb[si].dst = us_next[si];
+      sb[si].ilevel = t;
+      CUDA_TRY(launch_sparse(sb[si], WAVE_F32, s));
+    }
+    BatchArgs b;
+    memset(&b, 0, sizeof(b));
+    b.base = base;
+    b.base.acc_scale = -1.f;
+    for (int si = 0; si < nshots; ++si) {
+      if (shots[si].nt < t) continue;
+      b.cur[b.nshots] = static_cast<const float*>(us_cur[si]);
+      b.prev[b.nshots] = static_cast<float*>(us_next[si]);
+      b.accf[b.nshots] = 1;
+      if (++b.nshots == kMaxBatch) {
+        CUDA_TRY(run_batched(m, b, s));
+        b.nshots = 0;
+      }
+    }
+    if (b.nshots) CUDA_TRY(run_batched(m, b, s));
+    for (int si = 0; si < nshots; ++si) {
+      if (shots[si].nt < t) continue;
+      std::swap(us_cur[si], us_next[si]);
+    }
+  }
+  CUDA_TRY(launch_finish(g, w.acc, kd, 1.0 / dt, 1, opts->grad_wrt == WAVE_GRAD_PARAM, m->param, grad_dev, s));
+  if (k_dev) CUDA_TRY(cudaMemcpyAsync(k_dev, kd, sizeof(double), cudaMemcpyDeviceToDevice, s));
+  return WAVE_OK;
 }
+
 
 extern "C" wave_status wave_adjoint_sensitivity(wave_model m, const wave_shot* shots, int32_t nshots,
                                                 const wave_gradient_opts* opts, float* grad_dev,
@@ -529,6 +738,7 @@ extern "C" wave_status wave_adjoint_sensitivity(wave_model m, const wave_shot* s
   wave_gradient_workspace_size(m, shots, nshots, opts, &need);
   if (!ws || ws_bytes < need || reinterpret_cast<uintptr_t>(ws) % 256) return WAVE_EWORKSPACE;
   cudaStream_t s = (cudaStream_t)stream;
+  if (opts->batched) return gradient_batched(m, shots, nshots, opts, grad_dev, misfit_dev, k_dev, ws, s);
   const Geom& g = m->g;
   const int stor = m->d.storage;
   const size_t eb = storage_bytes(stor);

@@ -1,7 +1,16 @@
-// 3D fused leapfrog step, FP32 storage, orders 2-8: shared-memory plane ring
-// filled by cp.async.  Same arithmetic as the register-queue kernel
-// (Eq. FDstencil1 in squared-slowness form, sensitivity increment of
-// Algorithm 1 / Eq. kernel1) with a different mapping:
+// 3D fused leapfrog step, FP32 storage, orders 2-8, one or many shots per
+// launch: shared-memory plane ring filled by cp.async.  Same arithmetic as
+// the register-queue kernel (Eq. FDstencil1 in squared-slowness form,
+// sensitivity increment of Algorithm 1 / Eq. kernel1) with a different
+// mapping:
+//
+// * the grid runs z-blocks fastest, so vertically adjacent CTAs (which share
+//   r halo planes) run side by side and the halo planes come from L2;
+// * with several shots (batched mode), a CTA advances each listed shot in
+//   turn over its tile; the shots' increments go into the one accumulator
+//   K~ (summed over sources), whose tile stays in L2 between shots, so per
+//   shot and cell HBM sees u^n, u^{n-1}, u^{n+1} (12 B) and coef / acc only
+//   once per step for all shots;
 //
 // * a CTA of TY warps owns TY rows x 128 cells and marches up z over a block
 //   of planes;
@@ -41,23 +50,22 @@ struct Ring {
 
 template <int R, int TY, int D>
 __global__ void __launch_bounds__(TY * 32, (TY == 8 ? 2 : 1))
-step3d_velocity_ring_kernel(StepArgs a) {
+step3d_velocity_ring_kernel(BatchArgs b) {
   using RG = Ring<R, TY, D>;
   extern __shared__ __align__(16) float ring[];
+  const StepArgs& a = b.base;
   const Geom& g = a.g;
   const int tid = threadIdx.x;
   const int lane = tid & 31;
   const int warp = tid >> 5;
-  const int64_t x0 = (int64_t)blockIdx.x * kStrip;
-  const int64_t ty0 = (int64_t)blockIdx.y * TY;
-  const int64_t y = ty0 + warp;
-  const int z0 = (int)((int64_t)blockIdx.z * a.zblock);
+  const int z0 = (int)((int64_t)blockIdx.x * a.zblock);
   const int z1 = (int)min((int64_t)z0 + a.zblock, g.nz);
+  const int64_t x0 = (int64_t)blockIdx.y * kStrip;
+  const int64_t ty0 = (int64_t)blockIdx.z * TY;
+  const int64_t y = ty0 + warp;
   const int64_t xl = x0 + 4 * lane;
   const bool row_valid = y < g.ny;
   const bool xfix = (x0 == 0) || (x0 + kStrip + R > g.nx);
-  const float* __restrict__ uc = reinterpret_cast<const float*>(a.u_cur);
-  float* __restrict__ up = reinterpret_cast<float*>(a.u_prev);
   const int64_t row_off = y * g.px + xl;
 
   // Per-thread staging descriptors, fixed for the whole march: source row
@@ -86,139 +94,146 @@ step3d_velocity_ring_kernel(StepArgs a) {
     }
   }
 
-  // Stage plane p into ring slot `slot`; always commits one group.
-  auto issue = [&](int p, int slot) {
-    if (p < z1 + R) {
-      float zs;
-      const int64_t zsrc = mirror_index(p, g.nz, g.bc, &zs);
-      const float* src0 = uc + zsrc * g.plane;
-      float* dst0 = ring + slot * RG::PLANE;
-#pragma unroll
-      for (int k = 0; k < RG::K; ++k) {
-        if (c_dst[k] < 0) continue;
-        const float sgn = c_sgn[k] * zs;
-        float* dst = dst0 + c_dst[k];
-        if (sgn == 0.f) {
-          *reinterpret_cast<float4*>(dst) = make_float4(0.f, 0.f, 0.f, 0.f);
-        } else if (sgn > 0.f) {
-          cp_async16(dst, src0 + c_off[k]);
-        } else {
-          *reinterpret_cast<float4*>(dst) = f4_scale(__ldg(reinterpret_cast<const float4*>(src0 + c_off[k])), sgn);
+  for (int shot = 0; shot < b.nshots; ++shot) {
+    const float* __restrict__ uc = b.cur[shot];
+    float* __restrict__ up = b.prev[shot];
+    const bool acc_on = b.accf[shot] != 0;
+    // Stage plane p into ring slot `slot`; always commits one group.
+    auto issue = [&](int p, int slot) {
+      if (p < z1 + R) {
+        float zs;
+        const int64_t zsrc = mirror_index(p, g.nz, g.bc, &zs);
+        const float* src0 = uc + zsrc * g.plane;
+        float* dst0 = ring + slot * RG::PLANE;
+  #pragma unroll
+        for (int k = 0; k < RG::K; ++k) {
+          if (c_dst[k] < 0) continue;
+          const float sgn = c_sgn[k] * zs;
+          float* dst = dst0 + c_dst[k];
+          if (sgn == 0.f) {
+            *reinterpret_cast<float4*>(dst) = make_float4(0.f, 0.f, 0.f, 0.f);
+          } else if (sgn > 0.f) {
+            cp_async16(dst, src0 + c_off[k]);
+          } else {
+            *reinterpret_cast<float4*>(dst) = f4_scale(__ldg(reinterpret_cast<const float4*>(src0 + c_off[k])), sgn);
+          }
         }
       }
-    }
-    cp_async_commit();
-  };
+      cp_async_commit();
+    };
 
-  // prologue: planes z0-R .. z0+R+D-1 into slots 0 .. 2R+D-1
-#pragma unroll 1
-  for (int i = 0; i < 2 * R + D; ++i) issue(z0 - R + i, i);
-  int s0 = 0;  // slot of plane z - R
+    // prologue: planes z0-R .. z0+R+D-1 into slots 0 .. 2R+D-1 (drained and
+    // fenced by the __syncthreads at the end of the previous shot)
+  #pragma unroll 1
+    for (int i = 0; i < 2 * R + D; ++i) issue(z0 - R + i, i);
+    int s0 = 0;  // slot of plane z - R
 
-  float4 u_old = make_float4(0.f, 0.f, 0.f, 0.f), cf = u_old, ac = u_old, cp = u_old;
-  auto load_streams = [&](int z, float4& uo, float4& c, float4& acv, float4& cpv) {
-    const int64_t off = (int64_t)z * g.plane + row_off;
-    uo = *reinterpret_cast<const float4*>(up + off);
-    c = __ldg(reinterpret_cast<const float4*>(a.coef + off));
-    if (a.acc_mass) {
-      acv = *reinterpret_cast<const float4*>(a.acc + off);
-      if (a.comp) cpv = *reinterpret_cast<const float4*>(a.comp + off);
-    }
-  };
-  if (row_valid && z0 < z1) load_streams(z0, u_old, cf, ac, cp);
-
-  const int col = 4 + 4 * lane;
-  for (int z = z0; z < z1; ++z) {
-    cp_async_wait<D - 1>();
-    __syncthreads();
-    // plane z+R+D reuses the slot of plane z-R-1 (read last in iteration z-1)
-    {
-      int sn = s0 + 2 * R + D;
-      sn -= sn >= RG::P ? RG::P : 0;
-      issue(z + R + D, sn);
-    }
-    float4 n_old = u_old, n_cf = cf, n_ac = ac, n_cp = cp;
-    if (row_valid && z + 1 < z1) load_streams(z + 1, n_old, n_cf, n_ac, n_cp);
-    if (row_valid) {
-      int sl[2 * R + 1];   // slots of planes z-R .. z+R
-#pragma unroll
-      for (int j = 0; j <= 2 * R; ++j) {
-        const int t = s0 + j;
-        sl[j] = t >= RG::P ? t - RG::P : t;
-      }
-      const float* cplane = ring + sl[R] * RG::PLANE;
-      float* srow = const_cast<float*>(cplane) + (R + warp) * kRowW;
-      if (xfix) {
-        float val = 0.f;
-        int pos = -1;
-        int64_t gx = 0;
-        if (lane < R && x0 == 0) {
-          gx = -1 - lane;
-          pos = 3 - lane;
-        } else if (lane >= 8 && lane < 8 + R) {
-          gx = (g.nx < x0 + kStrip ? g.nx : x0 + kStrip) + (lane - 8);
-          if (gx >= g.nx) pos = (int)(gx - x0 + 4);
-        }
-        __syncwarp();
-        if (pos >= 0) {
-          float sx;
-          const int64_t m = mirror_index(gx, g.nx, g.bc, &sx);
-          val = sx == 0.f ? 0.f : sx * srow[m - x0 + 4];
-        }
-        __syncwarp();
-        if (pos >= 0) srow[pos] = val;
-        __syncwarp();
-      }
-      float lap[4];
-      x_terms<R>(srow, lane, lap, 3.f * cw<R>(0));
-      const float4 u = *reinterpret_cast<const float4*>(srow + 4 + 4 * lane);
-#pragma unroll
-      for (int j = 1; j <= R; ++j) {
-        const float4 ym = *reinterpret_cast<const float4*>(cplane + (R + warp - j) * kRowW + col);
-        const float4 yp = *reinterpret_cast<const float4*>(cplane + (R + warp + j) * kRowW + col);
-        const float4 zm = *reinterpret_cast<const float4*>(ring + sl[R - j] * RG::PLANE + (R + warp) * kRowW + col);
-        const float4 zp = *reinterpret_cast<const float4*>(ring + sl[R + j] * RG::PLANE + (R + warp) * kRowW + col);
-        const float c = cw<R>(j);
-        lap[0] = fmaf(c, (ym.x + yp.x) + (zm.x + zp.x), lap[0]);
-        lap[1] = fmaf(c, (ym.y + yp.y) + (zm.y + zp.y), lap[1]);
-        lap[2] = fmaf(c, (ym.z + yp.z) + (zm.z + zp.z), lap[2]);
-        lap[3] = fmaf(c, (ym.w + yp.w) + (zm.w + zp.w), lap[3]);
-      }
-      float4 un;
-      un.x = fmaf(cf.x, lap[0], 2.f * u.x - u_old.x);
-      un.y = fmaf(cf.y, lap[1], 2.f * u.y - u_old.y);
-      un.z = fmaf(cf.z, lap[2], 2.f * u.z - u_old.z);
-      un.w = fmaf(cf.w, lap[3], 2.f * u.w - u_old.w);
+    float4 u_old = make_float4(0.f, 0.f, 0.f, 0.f), cf = u_old, ac = u_old, cp = u_old;
+    auto load_streams = [&](int z, float4& uo, float4& c, float4& acv, float4& cpv) {
       const int64_t off = (int64_t)z * g.plane + row_off;
-      *reinterpret_cast<float4*>(up + off) = un;
-      if (a.acc_mass) {
-        const float d0 = un.x - u.x, d1 = un.y - u.y, d2 = un.z - u.z, d3 = un.w - u.w;
-        if (a.comp) {
-          kahan_add(ac.x, cp.x, a.acc_scale * d0 * d0);
-          kahan_add(ac.y, cp.y, a.acc_scale * d1 * d1);
-          kahan_add(ac.z, cp.z, a.acc_scale * d2 * d2);
-          kahan_add(ac.w, cp.w, a.acc_scale * d3 * d3);
-          *reinterpret_cast<float4*>(a.comp + off) = cp;
-        } else {
-          ac.x = fmaf(a.acc_scale * d0, d0, ac.x);
-          ac.y = fmaf(a.acc_scale * d1, d1, ac.y);
-          ac.z = fmaf(a.acc_scale * d2, d2, ac.z);
-          ac.w = fmaf(a.acc_scale * d3, d3, ac.w);
-        }
-        *reinterpret_cast<float4*>(a.acc + off) = ac;
+      uo = *reinterpret_cast<const float4*>(up + off);
+      c = __ldg(reinterpret_cast<const float4*>(a.coef + off));
+      if (acc_on) {
+        acv = *reinterpret_cast<const float4*>(a.acc + off);
+        if (a.comp) cpv = *reinterpret_cast<const float4*>(a.comp + off);
       }
+    };
+    if (row_valid && z0 < z1) load_streams(z0, u_old, cf, ac, cp);
+
+    const int col = 4 + 4 * lane;
+    for (int z = z0; z < z1; ++z) {
+      cp_async_wait<D - 1>();
+      __syncthreads();
+      // plane z+R+D reuses the slot of plane z-R-1 (read last in iteration z-1)
+      {
+        int sn = s0 + 2 * R + D;
+        sn -= sn >= RG::P ? RG::P : 0;
+        issue(z + R + D, sn);
+      }
+      float4 n_old = u_old, n_cf = cf, n_ac = ac, n_cp = cp;
+      if (row_valid && z + 1 < z1) load_streams(z + 1, n_old, n_cf, n_ac, n_cp);
+      if (row_valid) {
+        int sl[2 * R + 1];   // slots of planes z-R .. z+R
+  #pragma unroll
+        for (int j = 0; j <= 2 * R; ++j) {
+          const int t = s0 + j;
+          sl[j] = t >= RG::P ? t - RG::P : t;
+        }
+        const float* cplane = ring + sl[R] * RG::PLANE;
+        float* srow = const_cast<float*>(cplane) + (R + warp) * kRowW;
+        if (xfix) {
+          float val = 0.f;
+          int pos = -1;
+          int64_t gx = 0;
+          if (lane < R && x0 == 0) {
+            gx = -1 - lane;
+            pos = 3 - lane;
+          } else if (lane >= 8 && lane < 8 + R) {
+            gx = (g.nx < x0 + kStrip ? g.nx : x0 + kStrip) + (lane - 8);
+            if (gx >= g.nx) pos = (int)(gx - x0 + 4);
+          }
+          __syncwarp();
+          if (pos >= 0) {
+            float sx;
+            const int64_t m = mirror_index(gx, g.nx, g.bc, &sx);
+            val = sx == 0.f ? 0.f : sx * srow[m - x0 + 4];
+          }
+          __syncwarp();
+          if (pos >= 0) srow[pos] = val;
+          __syncwarp();
+        }
+        float lap[4];
+        x_terms<R>(srow, lane, lap, 3.f * cw<R>(0));
+        const float4 u = *reinterpret_cast<const float4*>(srow + 4 + 4 * lane);
+  #pragma unroll
+        for (int j = 1; j <= R; ++j) {
+          const float4 ym = *reinterpret_cast<const float4*>(cplane + (R + warp - j) * kRowW + col);
+          const float4 yp = *reinterpret_cast<const float4*>(cplane + (R + warp + j) * kRowW + col);
+          const float4 zm = *reinterpret_cast<const float4*>(ring + sl[R - j] * RG::PLANE + (R + warp) * kRowW + col);
+          const float4 zp = *reinterpret_cast<const float4*>(ring + sl[R + j] * RG::PLANE + (R + warp) * kRowW + col);
+          const float c = cw<R>(j);
+          lap[0] = fmaf(c, (ym.x + yp.x) + (zm.x + zp.x), lap[0]);
+          lap[1] = fmaf(c, (ym.y + yp.y) + (zm.y + zp.y), lap[1]);
+          lap[2] = fmaf(c, (ym.z + yp.z) + (zm.z + zp.z), lap[2]);
+          lap[3] = fmaf(c, (ym.w + yp.w) + (zm.w + zp.w), lap[3]);
+        }
+        float4 un;
+        un.x = fmaf(cf.x, lap[0], 2.f * u.x - u_old.x);
+        un.y = fmaf(cf.y, lap[1], 2.f * u.y - u_old.y);
+        un.z = fmaf(cf.z, lap[2], 2.f * u.z - u_old.z);
+        un.w = fmaf(cf.w, lap[3], 2.f * u.w - u_old.w);
+        const int64_t off = (int64_t)z * g.plane + row_off;
+        *reinterpret_cast<float4*>(up + off) = un;
+        if (acc_on) {
+          const float d0 = un.x - u.x, d1 = un.y - u.y, d2 = un.z - u.z, d3 = un.w - u.w;
+          if (a.comp) {
+            kahan_add(ac.x, cp.x, a.acc_scale * d0 * d0);
+            kahan_add(ac.y, cp.y, a.acc_scale * d1 * d1);
+            kahan_add(ac.z, cp.z, a.acc_scale * d2 * d2);
+            kahan_add(ac.w, cp.w, a.acc_scale * d3 * d3);
+            *reinterpret_cast<float4*>(a.comp + off) = cp;
+          } else {
+            ac.x = fmaf(a.acc_scale * d0, d0, ac.x);
+            ac.y = fmaf(a.acc_scale * d1, d1, ac.y);
+            ac.z = fmaf(a.acc_scale * d2, d2, ac.z);
+            ac.w = fmaf(a.acc_scale * d3, d3, ac.w);
+          }
+          *reinterpret_cast<float4*>(a.acc + off) = ac;
+        }
+      }
+      u_old = n_old;
+      cf = n_cf;
+      ac = n_ac;
+      cp = n_cp;
+      s0 = s0 + 1 == RG::P ? 0 : s0 + 1;
     }
-    u_old = n_old;
-    cf = n_cf;
-    ac = n_ac;
-    cp = n_cp;
-    s0 = s0 + 1 == RG::P ? 0 : s0 + 1;
+    cp_async_wait<0>();
+    __syncthreads();  // the ring is refilled for the next shot
   }
-  cp_async_wait<0>();
 }
 
 template <int R, int TY, int D>
-static cudaError_t launch_ring(const StepArgs& a, cudaStream_t s) {
+static cudaError_t launch_ring(const BatchArgs& a, cudaStream_t s) {
   using RG = Ring<R, TY, D>;
   static bool configured = false;
   if (!configured) {
@@ -227,28 +242,39 @@ static cudaError_t launch_ring(const StepArgs& a, cudaStream_t s) {
     if (e != cudaSuccess) return e;
     configured = true;
   }
-  const Geom& g = a.g;
-  dim3 grid((unsigned)((g.nx + kStrip - 1) / kStrip), (unsigned)((g.ny + TY - 1) / TY),
-            (unsigned)((g.nz + a.zblock - 1) / a.zblock));
+  const Geom& g = a.base.g;
+  dim3 grid((unsigned)((g.nz + a.base.zblock - 1) / a.base.zblock), (unsigned)((g.nx + kStrip - 1) / kStrip),
+            (unsigned)((g.ny + TY - 1) / TY));
   step3d_velocity_ring_kernel<R, TY, D><<<grid, TY * 32, RG::bytes(), s>>>(a);
   count_launch();
   return cudaGetLastError();
 }
 
 template <int R>
-static cudaError_t launch_ring_r(const StepArgs& a, cudaStream_t s) {
-  if (a.tile_rows == 16) return a.ring_depth == 2 ? launch_ring<R, 16, 2>(a, s) : launch_ring<R, 16, 3>(a, s);
-  return a.ring_depth == 2 ? launch_ring<R, 8, 2>(a, s) : launch_ring<R, 8, 3>(a, s);
+static cudaError_t launch_ring_r(const BatchArgs& a, cudaStream_t s) {
+  if (a.base.tile_rows == 16)
+    return a.base.ring_depth == 2 ? launch_ring<R, 16, 2>(a, s) : launch_ring<R, 16, 3>(a, s);
+  return a.base.ring_depth == 2 ? launch_ring<R, 8, 2>(a, s) : launch_ring<R, 8, 3>(a, s);
+}
+
+cudaError_t launch_step3d_batched(const BatchArgs& b, int order, cudaStream_t s) {
+  switch (order) {
+    case 2: return launch_ring_r<1>(b, s);
+    case 4: return launch_ring_r<2>(b, s);
+    case 6: return launch_ring_r<3>(b, s);
+    case 8: return launch_ring_r<4>(b, s);
+  }
+  return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_step3d_ring(const StepArgs& a, int order, cudaStream_t s) {
-  switch (order) {
-    case 2: return launch_ring_r<1>(a, s);
-    case 4: return launch_ring_r<2>(a, s);
-    case 6: return launch_ring_r<3>(a, s);
-    case 8: return launch_ring_r<4>(a, s);
-  }
-  return cudaErrorInvalidValue;
+  BatchArgs b;
+  b.base = a;
+  b.nshots = 1;
+  b.cur[0] = reinterpret_cast<const float*>(a.u_cur);
+  b.prev[0] = reinterpret_cast<float*>(a.u_prev);
+  b.accf[0] = a.acc_mass;
+  return launch_step3d_batched(b, order, s);
 }
 
 }  // namespace wave

@@ -140,6 +140,19 @@ cudaError_t launch_step_velocity(const StepArgs& a, int order, int storage, cuda
 cudaError_t launch_step_density(const StepArgs& a, int storage, cudaStream_t s);
 cudaError_t launch_step3d_ring(const StepArgs& a, int order, cudaStream_t s);
 
+// Batched 3D step: every listed shot advances one step; the shots' sensitivity
+// increments are summed per cell before one accumulator update.
+constexpr int kMaxBatch = 32;
+struct BatchArgs {
+  StepArgs base;                 // geometry, coef, acc, comp, acc_scale, zblock, ring_depth
+  int nshots;
+  const float* cur[kMaxBatch];   // level n of each shot
+  float* prev[kMaxBatch];        // level n-1 -> n+1 of each shot
+  int accf[kMaxBatch];           // accumulate this shot's increment this step
+};
+cudaError_t launch_step3d_batched(const BatchArgs& b, int order, cudaStream_t s);
+
+
 // ---- sparse (source / receiver) kernel -----------------------------------
 struct SparseArgs {
   const void* gsrc;       // buffer holding level `glevel` (gather), or null

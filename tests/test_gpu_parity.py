@@ -332,3 +332,56 @@ def test_kernels_run_through_the_library(W):
     m.gradient(gpu_shots(W, prob))
     torch.cuda.synchronize()
     assert W.launch_count() - before >= 4 * 10
+
+
+# ---------------------------------------------------------------------------
+# batched multi-shot path
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("order,kahan", [(8, False), (4, True), (2, False)])
+def test_batched_matches_oracle_and_plain(W, order, kahan):
+    shape = (21, 19, 140)
+    prob = make_problem(shape, order, "dirichlet", nshots=3, nt_list=[40, 55, 47], nrec=30, seed=21)
+    m = gpu_model(W, prob, kahan=kahan)
+    # All shots share one k (fixed from the first shot); these random shots
+    # differ a lot in residual size, so a larger ratio keeps every shot's
+    # k u_adj / u above the FP32 cancellation floor (Sec. 4.1).
+    gb, mb, kb = m.gradient(gpu_shots(W, prob), batched=True, k_ratio=0.1)
+    gp, mp, kp = m.gradient(gpu_shots(W, prob), batched=False, k=float(kb.item()))
+    torch.cuda.synchronize()
+    k = float(kb.item())
+    med = prob.medium()
+    kt = np.zeros(shape)
+    c = 0.0
+    for s, n in zip(prob.oracle_shots(), prob.nt):
+        r = O.superposition_gradient(med, [s], n, k)
+        kt += r["K_tilde"]
+        c += r["C"]
+    eb, ep = rel_l2(gb.cpu().numpy(), kt), rel_l2(gp.cpu().numpy(), kt)
+    print(f"\nbatched o{order} kahan={kahan}: batched {eb:.2e}, plain {ep:.2e} vs oracle")
+    assert eb < GRAD_TOL and ep < GRAD_TOL
+    assert abs(float(mb.item()) - c) < MISFIT_TOL * abs(c)
+    assert rel_l2(gb.cpu().numpy(), gp.cpu().numpy()) < 1e-4
+    assert float(mb.item()) == float(mp.item())
+
+
+def test_batched_more_shots_than_one_launch_holds(W):
+    shape = (12, 13, 130)
+    n = 34
+    prob = make_problem(shape, 2, "neumann", nshots=n, nt_list=[30 + (i % 5) for i in range(n)], nrec=60, seed=22)
+    # Kahan on: batched mode sums every shot's forward increments before the
+    # superposed passes subtract theirs, so without compensation its FP32
+    # accumulation error grows with the number of shots.
+    m = gpu_model(W, prob, kahan=True)
+    gb, mb, kb = m.gradient(gpu_shots(W, prob), batched=True, k_ratio=0.1)
+    gp, mp, _ = m.gradient(gpu_shots(W, prob), batched=False, k=float(kb.item()))
+    torch.cuda.synchronize()
+    assert rel_l2(gb.cpu().numpy(), gp.cpu().numpy()) < 1e-4
+    assert abs(float(mb.item()) - float(mp.item())) <= 1e-12 * abs(float(mp.item()))
+
+
+def test_batched_rejects_unsupported_layouts(W):
+    prob = make_problem((40, 130), 4, nt=10, seed=1)
+    m = gpu_model(W, prob)
+    with pytest.raises(W.WaveError) as e:
+        m.gradient(gpu_shots(W, prob), batched=True)
+    assert e.value.status == 7
