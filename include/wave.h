@@ -196,8 +196,9 @@ wave_status wave_forward(wave_model model, const wave_shot* shots, int32_t nshot
  * accumulating +K(u^s,u^s); K~ = difference / 2k (Eq. superposedkernel).
  * grad_dev: dense FP32 grid, summed over shots, w.r.t. opts->grad_wrt.
  * misfit_dev: one double, C summed over shots.  k_dev: one double, the k used
- * (all shots share it).  Exact mode stores the forward history instead and
- * returns the standard adjoint gradient. */
+ * (all shots share it).  Exact mode (velocity form, FP32 storage, one shot at
+ * a time) stores the forward history u^0..u^{N+1} instead and returns the
+ * standard adjoint gradient; k_dev then receives 0. */
 wave_status wave_gradient_workspace_size(wave_model model, const wave_shot* shots, int32_t nshots,
                                          const wave_gradient_opts* opts, size_t* bytes);
 wave_status wave_adjoint_sensitivity(wave_model model, const wave_shot* shots, int32_t nshots,

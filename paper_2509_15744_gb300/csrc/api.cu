@@ -389,6 +389,7 @@ static SparseArgs sparse_args(const wave_model_s* m, const int64_t* recp, int32_
   a.ilevel = 0;
   a.coef = m->coef;
   a.h2 = (float)(m->d.h * m->d.h);
+  a.inj_sign = -1.f;
   return a;
 }
 
@@ -518,7 +519,9 @@ static wave_status validate_opts(const wave_model_s* m, const wave_gradient_opts
   if (o->objective != WAVE_OBJ_L2 && o->objective != WAVE_OBJ_PATCH) return WAVE_EINVAL;
   if (o->mode != WAVE_SUPERPOSITION && o->mode != WAVE_EXACT_STORED) return WAVE_EINVAL;
   if (o->grad_wrt != WAVE_GRAD_MASS && o->grad_wrt != WAVE_GRAD_PARAM) return WAVE_EINVAL;
-  if (o->mode == WAVE_EXACT_STORED) return WAVE_EUNSUPPORTED;
+  if (o->mode == WAVE_EXACT_STORED &&
+      (o->batched || m->d.physics != WAVE_VELOCITY || m->d.storage != WAVE_F32))
+    return WAVE_EUNSUPPORTED;
   if (o->batched && !(m->d.ndim == 3 && m->d.physics == WAVE_VELOCITY && m->d.storage == WAVE_F32))
     return WAVE_EUNSUPPORTED;
   return WAVE_OK;
@@ -557,6 +560,37 @@ static void carve_batched(Carve& c, const wave_model_s* m, const wave_shot* shot
   w->scal = c.take<double>(4);
 }
 
+// Exact mode: the forward history u^0..u^{N+1} of one shot at a time.
+struct ExactWs {
+  float* acc;
+  float* hist;
+  float* lam0;
+  float* lam1;
+  float* resid;
+  int64_t* recp;
+  double* parts;
+  double* scal;
+};
+
+static void carve_exact(Carve& c, const wave_model_s* m, const wave_shot* shots, int32_t nshots, ExactWs* w) {
+  int nmax = 1;
+  int64_t maxres = 1;
+  int32_t maxrec = 1;
+  for (int s = 0; s < nshots; ++s) {
+    nmax = std::max(nmax, shots[s].nt);
+    maxres = std::max<int64_t>(maxres, (int64_t)(shots[s].nt + 1) * shots[s].nrec);
+    maxrec = std::max(maxrec, shots[s].nrec);
+  }
+  w->acc = c.take<float>(m->g.cells);
+  w->hist = c.take<float>((size_t)(nmax + 2) * m->g.cells);
+  w->lam0 = c.take<float>(m->g.cells);
+  w->lam1 = c.take<float>(m->g.cells);
+  w->resid = c.take<float>(maxres);
+  w->recp = c.take<int64_t>(maxrec);
+  w->parts = c.take<double>(1024);
+  w->scal = c.take<double>(4);
+}
+
 extern "C" wave_status wave_gradient_workspace_size(wave_model m, const wave_shot* shots, int32_t nshots,
                                                     const wave_gradient_opts* opts, size_t* bytes) {
   if (!m || !bytes) return WAVE_EINVAL;
@@ -565,7 +599,10 @@ extern "C" wave_status wave_gradient_workspace_size(wave_model m, const wave_sho
   st = validate_opts(m, opts);
   if (st != WAVE_OK) return st;
   Carve c(nullptr);
-  if (opts->batched) {
+  if (opts->mode == WAVE_EXACT_STORED) {
+    ExactWs w;
+    carve_exact(c, m, shots, nshots, &w);
+  } else if (opts->batched) {
     BatchWs w;
     carve_batched(c, m, shots, nshots, &w);
   } else {
@@ -573,6 +610,93 @@ extern "C" wave_status wave_gradient_workspace_size(wave_model m, const wave_sho
     carve_gradient(c, m, shots, nshots, &w);
   }
   *bytes = c.off;
+  return WAVE_OK;
+}
+
+// Standard adjoint over the stored forward history (Sec. 2.2 sensitivity
+// analysis): forward with every level kept, then the adjoint recursion
+// lambda^{j-1} = 2 lambda^j - lambda^{j+1} + dt^2/a (L lambda^j + f_adj^j) from
+// lambda^{N+1} = lambda^N = 0, accumulating -(lambda^j - lambda^{j-1})(u^j - u^{j-1})
+// (dt times the discrete Eq. kernel1).  The comparator of the superposition
+// result; memory grows with N.
+static wave_status gradient_exact(wave_model m, const wave_shot* shots, int32_t nshots,
+                                  const wave_gradient_opts* opts, float* grad_dev, double* misfit_dev,
+                                  double* k_dev, void* ws, cudaStream_t s) {
+  const Geom& g = m->g;
+  const double dt = m->d.dt;
+  Carve c(ws);
+  ExactWs w;
+  carve_exact(c, m, shots, nshots, &w);
+  double* kd = w.scal + 0;
+  double* misfit_acc = misfit_dev ? misfit_dev : w.scal + 3;
+  CUDA_TRY(cudaMemsetAsync(w.acc, 0, g.cells * sizeof(float), s));
+  CUDA_TRY(cudaMemsetAsync(misfit_acc, 0, sizeof(double), s));
+  CUDA_TRY(launch_set_k(kd, 1.0, s));  // the adjoint source enters unscaled
+  auto level = [&](int n) { return w.hist + (size_t)n * g.cells; };
+  for (int si = 0; si < nshots; ++si) {
+    const wave_shot& sh = shots[si];
+    const int N = sh.nt;
+    const double wgt = objective_weight(opts, sh);
+    CUDA_TRY(launch_pitch_indices(g, sh.rec_cells_dev, sh.nrec, w.recp, s));
+    CUDA_TRY(cudaMemsetAsync(level(0), 0, 2 * g.cells * sizeof(float), s));
+    SparseArgs gat = sparse_args(m, w.recp, sh.nrec);
+    gat.observed = sh.observed_dev;
+    gat.obs_ld = N + 1;
+    gat.resid = w.resid;
+    gat.gsrc = level(0);
+    gat.glevel = 0;
+    CUDA_TRY(launch_sparse(gat, WAVE_F32, s));
+    gat.gsrc = level(1);
+    gat.glevel = 1;
+    CUDA_TRY(launch_sparse(gat, WAVE_F32, s));
+    SparseArgs inj = sparse_args(m, w.recp, 0);
+    inj.src_p = pitched_cell(g, sh.src_cell);
+    inj.wavelet = sh.wavelet_dev;
+    inj.inj_sign = 1.f;  // add f^n to the level the step just wrote
+    for (int n = 1; n <= N; ++n) {
+      StepArgs a = step_args(m, level(n), level(n - 1));
+      a.u_out = level(n + 1);
+      CUDA_TRY(run_step(m, a, s));
+      inj.dst = level(n + 1);
+      inj.ilevel = n;
+      CUDA_TRY(launch_sparse(inj, WAVE_F32, s));
+      if (n + 1 <= N) {
+        gat.gsrc = level(n + 1);
+        gat.glevel = n + 1;
+        CUDA_TRY(launch_sparse(gat, WAVE_F32, s));
+      }
+    }
+    const int64_t nres = (int64_t)(N + 1) * sh.nrec;
+    if (nres > 0) {
+      const int np = reduce_parts(nres);
+      CUDA_TRY(launch_sumsq_partial(w.resid, nullptr, nres, w.parts, np, s));
+      CUDA_TRY(launch_sum_final(w.parts, np, 0.5 * wgt * dt, 1, misfit_acc, s));
+    }
+    // adjoint: lambda^{N+1} = lambda^N = 0
+    CUDA_TRY(cudaMemsetAsync(w.lam0, 0, g.cells * sizeof(float), s));
+    CUDA_TRY(cudaMemsetAsync(w.lam1, 0, g.cells * sizeof(float), s));
+    float* lam_next = w.lam0;  // lambda^{j+1}
+    float* lam_cur = w.lam1;   // lambda^j
+    SparseArgs adj = sparse_args(m, w.recp, sh.nrec);
+    adj.resid_in = w.resid;
+    adj.k_dev = kd;
+    adj.weight = (float)wgt;
+    for (int j = N; j >= 1; --j) {
+      adj.dst = lam_next;
+      adj.ilevel = j;
+      CUDA_TRY(launch_sparse(adj, WAVE_F32, s));
+      StepArgs a = step_args(m, lam_cur, lam_next);
+      a.acc = w.acc;
+      a.acc_scale = -1.f;
+      a.acc_mass = 1;
+      a.mix_a = level(j);
+      a.mix_b = level(j - 1);
+      CUDA_TRY(run_step(m, a, s));
+      std::swap(lam_cur, lam_next);  // lam_cur = lambda^{j-1}
+    }
+  }
+  CUDA_TRY(launch_finish(g, w.acc, kd, 1.0 / dt, 0, opts->grad_wrt == WAVE_GRAD_PARAM, m->param, grad_dev, s));
+  if (k_dev) CUDA_TRY(cudaMemsetAsync(k_dev, 0, sizeof(double), s));
   return WAVE_OK;
 }
 
@@ -738,6 +862,7 @@ extern "C" wave_status wave_adjoint_sensitivity(wave_model m, const wave_shot* s
   wave_gradient_workspace_size(m, shots, nshots, opts, &need);
   if (!ws || ws_bytes < need || reinterpret_cast<uintptr_t>(ws) % 256) return WAVE_EWORKSPACE;
   cudaStream_t s = (cudaStream_t)stream;
+  if (opts->mode == WAVE_EXACT_STORED) return gradient_exact(m, shots, nshots, opts, grad_dev, misfit_dev, k_dev, ws, s);
   if (opts->batched) return gradient_batched(m, shots, nshots, opts, grad_dev, misfit_dev, k_dev, ws, s);
   const Geom& g = m->g;
   const int stor = m->d.storage;

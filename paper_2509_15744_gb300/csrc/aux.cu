@@ -227,12 +227,12 @@ __global__ void sparse_kernel(SparseArgs a) {
       const float e = a.resid_in[(int64_t)a.ilevel * a.nrec + t];
       const float inj = a.coef[p] * a.h2;
       const float kw = (float)(*a.k_dev) * a.weight;
-      Stor<T>::atomic_add(reinterpret_cast<T*>(a.dst) + p, inj * (kw * e));
+      Stor<T>::atomic_add(reinterpret_cast<T*>(a.dst) + p, -a.inj_sign * inj * (kw * e));
     }
   } else if (t == a.nrec) {
     if (a.dst != nullptr && a.src_p >= 0 && a.wavelet != nullptr) {
       const float inj = a.coef[a.src_p] * a.h2;
-      Stor<T>::atomic_add(reinterpret_cast<T*>(a.dst) + a.src_p, -inj * a.wavelet[a.ilevel]);
+      Stor<T>::atomic_add(reinterpret_cast<T*>(a.dst) + a.src_p, a.inj_sign * inj * a.wavelet[a.ilevel]);
     }
   }
 }

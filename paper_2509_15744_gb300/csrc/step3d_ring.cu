@@ -203,8 +203,16 @@ step3d_velocity_ring_kernel(BatchArgs b) {
         un.z = fmaf(cf.z, lap[2], 2.f * u.z - u_old.z);
         un.w = fmaf(cf.w, lap[3], 2.f * u.w - u_old.w);
         const int64_t off = (int64_t)z * g.plane + row_off;
-        *reinterpret_cast<float4*>(up + off) = un;
-        if (acc_on) {
+        *reinterpret_cast<float4*>((a.u_out ? reinterpret_cast<float*>(a.u_out) : up) + off) = un;
+        if (a.mix_a) {  // exact mode (one shot): acc += acc_scale (u_cur - u_next)(mix_a - mix_b)
+          const float4 ma = *reinterpret_cast<const float4*>(a.mix_a + off);
+          const float4 mb = *reinterpret_cast<const float4*>(a.mix_b + off);
+          ac.x = fmaf(a.acc_scale * (u.x - un.x), ma.x - mb.x, ac.x);
+          ac.y = fmaf(a.acc_scale * (u.y - un.y), ma.y - mb.y, ac.y);
+          ac.z = fmaf(a.acc_scale * (u.z - un.z), ma.z - mb.z, ac.z);
+          ac.w = fmaf(a.acc_scale * (u.w - un.w), ma.w - mb.w, ac.w);
+          *reinterpret_cast<float4*>(a.acc + off) = ac;
+        } else if (acc_on) {
           const float d0 = un.x - u.x, d1 = un.y - u.y, d2 = un.z - u.z, d3 = un.w - u.w;
           if (a.comp) {
             kahan_add(ac.x, cp.x, a.acc_scale * d0 * d0);

@@ -31,8 +31,18 @@ __device__ __forceinline__ void update_store(const StepArgs& a, int64_t off, con
   un.y = fmaf(cf.y, lap[1], 2.f * u.y - u_old.y);
   un.z = fmaf(cf.z, lap[2], 2.f * u.z - u_old.z);
   un.w = fmaf(cf.w, lap[3], 2.f * u.w - u_old.w);
-  Stor<T>::st4(reinterpret_cast<T*>(a.u_prev) + off, un);
-  if (a.acc_mass) {
+  Stor<T>::st4(reinterpret_cast<T*>(a.u_out ? a.u_out : a.u_prev) + off, un);
+  if (a.mix_a) {  // exact mode: acc += acc_scale (u_cur - u_next)(mix_a - mix_b)
+    const float4 ma = *reinterpret_cast<const float4*>(a.mix_a + off);
+    const float4 mb = *reinterpret_cast<const float4*>(a.mix_b + off);
+    float4* accp = reinterpret_cast<float4*>(a.acc + off);
+    float4 ac = *accp;
+    ac.x = fmaf(a.acc_scale * (u.x - un.x), ma.x - mb.x, ac.x);
+    ac.y = fmaf(a.acc_scale * (u.y - un.y), ma.y - mb.y, ac.y);
+    ac.z = fmaf(a.acc_scale * (u.z - un.z), ma.z - mb.z, ac.z);
+    ac.w = fmaf(a.acc_scale * (u.w - un.w), ma.w - mb.w, ac.w);
+    *accp = ac;
+  } else if (a.acc_mass) {
     const float4 ur = round_to_storage<T>(un);
     const float d0 = ur.x - u.x, d1 = ur.y - u.y, d2 = ur.z - u.z, d3 = ur.w - u.w;
     float4* accp = reinterpret_cast<float4*>(a.acc + off);

@@ -133,6 +133,10 @@ struct StepArgs {
   int64_t zblock;        // cells of the march axis per CTA (3D) / warp (2D)
   int tile_rows;         // 3D ring kernel: rows per CTA (8 or 16)
   int ring_depth;        // 3D ring kernel: planes copied ahead (2 or 3)
+  // Exact (stored-history) mode, FP32 velocity only:
+  void* u_out;           // output level (nullable: overwrite u_prev)
+  const float* mix_a;    // stored u^j (nullable): accumulate the mixed term
+  const float* mix_b;    // stored u^{j-1}: acc += acc_scale (u_cur - u_next)(mix_a - mix_b)
 };
 
 // Launchers (defined in step_*.cu).  Return cudaGetLastError() of the launch.
@@ -173,6 +177,9 @@ struct SparseArgs {
   const float* resid_in;  // time-major residuals of level ilevel (receivers), nullable
   const double* k_dev;    // superposition factor
   float weight;           // objective weight w (f_adj = -w e)
+  float inj_sign;         // -1: pre-subtract the force of the coming step from
+                          //     the level it overwrites; +1: add the force of
+                          //     the step just taken to its output level
 };
 cudaError_t launch_sparse(const SparseArgs& a, int storage, cudaStream_t s);
 

@@ -385,3 +385,34 @@ def test_batched_rejects_unsupported_layouts(W):
     with pytest.raises(W.WaveError) as e:
         m.gradient(gpu_shots(W, prob), batched=True)
     assert e.value.status == 7
+
+
+# ---------------------------------------------------------------------------
+# exact (stored-history) adjoint comparator
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("shape,order,bc,nshots", [((128, 128), 2, "dirichlet", 1), ((37, 150), 8, "neumann", 2),
+                                                   ((14, 17, 133), 4, "dirichlet", 1)])
+def test_exact_mode_matches_oracle_adjoint(W, shape, order, bc, nshots):
+    prob = make_problem(shape, order, bc, nt=120, nrec=40, seed=41, nshots=nshots)
+    m = gpu_model(W, prob)
+    ge, me, _ = m.gradient(gpu_shots(W, prob), mode="exact")
+    gs, ms, ks = m.gradient(gpu_shots(W, prob))
+    torch.cuda.synchronize()
+    c_ref, g_ref, _ = O.exact_gradient(prob.medium(), prob.oracle_shots(), prob.nt[0])
+    err = rel_l2(ge.cpu().numpy(), g_ref)
+    gap = rel_l2(gs.cpu().numpy(), ge.cpu().numpy())
+    print(f"\nexact mode {shape} o{order}: vs oracle adjoint {err:.2e}; superposition gap on GPU {gap:.2e}")
+    assert err < GRAD_TOL
+    assert abs(float(me.item()) - c_ref) < MISFIT_TOL * c_ref
+    assert abs(float(me.item()) - float(ms.item())) < 1e-5 * abs(float(ms.item()))
+    assert gap < 0.1
+
+
+def test_exact_mode_param_gradient(W):
+    prob = make_problem((30, 140), 4, "dirichlet", nt=80, nrec=30, seed=42)
+    m = gpu_model(W, prob)
+    gv, _, _ = m.gradient(gpu_shots(W, prob), mode="exact", grad_wrt="param")
+    torch.cuda.synchronize()
+    med = prob.medium()
+    _, g_ref, _ = O.exact_gradient(med, prob.oracle_shots(), prob.nt[0])
+    assert rel_l2(gv.cpu().numpy(), med.param_chain(g_ref)) < GRAD_TOL
