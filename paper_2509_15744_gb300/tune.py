@@ -1,0 +1,88 @@
+"""Autotuner for the step kernel's tiling, with a JSON cache.
+
+The tiling (`wave_model_set_tiling`: z-block depth, rows per CTA, ring
+depth) changes speed only, never results.  `tune()` times a short forward
+pass of the given shots with each candidate (CUDA events inside libwave,
+`wave_timing_*`), keeps the fastest, applies it to the model and caches it
+under a key of (dims, shape, order, physics, storage, shots per launch).
+"""
+from __future__ import annotations
+
+import json
+import os
+from typing import Dict, Optional, Sequence
+
+import torch
+
+from . import wave as W
+
+CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "tune_cache.json")
+
+
+def candidates(ndim: int, nz: int):
+    if ndim == 2:
+        return [(zb, 8, 3) for zb in (8, 16, 32, 64, 128) if zb <= max(8, nz)]
+    out = []
+    for rows in (8, 16):
+        for depth in (2, 3):
+            for zb in (16, 32, 64, 128):
+                if zb <= max(16, nz):
+                    out.append((zb, rows, depth))
+    return out
+
+
+def _key(model: W.Model, batch: int) -> str:
+    return json.dumps([len(model.shape), list(model.shape), model.order, model.physics, model.storage, batch])
+
+
+def _load() -> Dict[str, list]:
+    try:
+        with open(CACHE) as fh:
+            return json.load(fh)
+    except (OSError, ValueError):
+        return {}
+
+
+def _save(cache: Dict[str, list]):
+    os.makedirs(os.path.dirname(CACHE), exist_ok=True)
+    tmp = CACHE + ".tmp"
+    with open(tmp, "w") as fh:
+        json.dump(cache, fh, indent=1)
+    os.replace(tmp, CACHE)
+
+
+def tune(model: W.Model, shots: Sequence[W.Shot], steps: int = 12, batched: bool = False,
+         use_cache: bool = True, verbose: bool = False) -> tuple:
+    """Pick and apply the fastest tiling for this model and shot set."""
+    batch = len(shots) if batched else 1
+    key = _key(model, batch)
+    cache = _load() if use_cache else {}
+    if key in cache:
+        best = tuple(cache[key])
+        model.set_tiling(*best)
+        return best
+    dev = model.param.device
+    probe = []
+    for s in (shots if batched else shots[:1]):
+        n = min(steps, s.nt)
+        probe.append(W.Shot(s.src, s.wavelet[:n + 1].contiguous(), s.rec,
+                            None if s.observed is None else s.observed[:, :n + 1].contiguous()))
+    nz = model.shape[0]
+    results = []
+    for cand in candidates(len(model.shape), nz):
+        model.set_tiling(*cand)
+        model.gradient(probe, batched=batched, k=1.0)          # warm-up (and attribute setup)
+        torch.cuda.synchronize(dev)
+        W.timing_enable(True)
+        model.gradient(probe, batched=batched, k=1.0)
+        ms, n, _ = W.timing_read()
+        W.timing_enable(False)
+        results.append((ms / max(n, 1), cand))
+        if verbose:
+            print(f"tiling {cand}: {ms / max(n, 1):.4f} ms per step launch")
+    best = min(results)[1]
+    model.set_tiling(*best)
+    if use_cache:
+        cache[key] = list(best)
+        _save(cache)
+    return best
