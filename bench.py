@@ -81,6 +81,20 @@ def units_of(wl):
     return float(sum(wl.ncells * n for n in wl.nt))
 
 
+def aggregate(ms_local, units_local, dist=None, device=None):
+    """Whole-job timing over ranks: the slowest rank's time and the sum of the
+    units every rank processed (replicas: each rank runs its own copy of the
+    workload, so there is no exchange on the data path)."""
+    if dist is None:
+        return ms_local, units_local
+    import torch
+    t = torch.tensor([ms_local], dtype=torch.float64, device=device)
+    u = torch.tensor([units_local], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
 # ---------------------------------------------------------------------------
 # CPU oracle sample (cpu_baseline leg and the reference arm)
 # ---------------------------------------------------------------------------
@@ -243,7 +257,8 @@ def main():
 
     wl = make_workload(args.workload, args.shape, args.shots, args.nt)
     dt = W.cfl_dt(wl.ndim, wl.order, wl.h, wl.vmax, wl.cfl_fraction)
-    mode = "plain" if args.mode in ("auto", "plain") else "batched"
+    batched_ok = wl.ndim == 3 and wl.physics == "velocity" and wl.nshots > 1
+    mode = args.mode if args.mode != "auto" else ("batched" if batched_ok else "plain")
 
     def barrier():
         torch.cuda.synchronize()
@@ -266,6 +281,8 @@ def main():
     shots = [W.Shot(wl.sources[i], wavs[i], recs[i], observed[i]) for i in range(wl.nshots)]
     model = W.Model(param0, wl.h, dt, wl.order, wl.physics, wl.bc, kahan=args.kahan)
     gkw = dict(objective=wl.objective, patch_sign=wl.patch_sign, batched=(mode == "batched"))
+    from paper_2509_15744_gb300 import tune
+    tiling = tune.tune(model, shots, batched=(mode == "batched"))
 
     # ---- warm-up -----------------------------------------------------------
     for _ in range(args.warmup):
@@ -290,11 +307,7 @@ def main():
     W.timing_enable(False)
     launches = W.launch_count() - launches0
     clk = clocks.stop()
-    if dist is not None:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    units = units_of(wl) * world
+    ms, units = aggregate(ms, units_of(wl), dist, dev)
     value = units * args.steps / (ms / 1e3) / 1e9
     grad_norm = float(torch.linalg.vector_norm(grad.double()).item())
     misfit_val = float(mis.item())
@@ -338,18 +351,19 @@ def main():
             h_mis.copy_(mi2, non_blocking=True)
             torch.cuda.synchronize()
         barrier()
-        el = time.perf_counter() - t0
-        if dist is not None:
-            t = torch.tensor([el], device=dev, dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            el = float(t.item())
+        el, _ = aggregate(time.perf_counter() - t0, 0.0, dist, dev)
         e2e = {"value": units * args.steps / el / 1e9, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h)}
 
     # ---- roofline of the dominant kernel (the fused step) ---------------------
     peak, peak_kind = measured_peak()
     achieved = step_bytes / (step_ms / 1e3) / 1e9 if step_ms > 0 else 0.0
-    kfile = "step_velocity.cu" if wl.physics == "velocity" else "step_density.cu"
+    if wl.physics == "density":
+        kfile = "step_density.cu"
+    elif wl.ndim == 3:
+        kfile = "step3d_ring.cu"
+    else:
+        kfile = "step_velocity.cu"
     traffic = kernel_traffic(kfile, wl.name)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "peak_source": peak_kind,
@@ -371,7 +385,7 @@ def main():
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": wl.name, "shape": list(wl.shape), "order": wl.order, "physics": wl.physics,
                        "shots": wl.nshots, "nt_total": int(sum(wl.nt)), "mode": mode, "kahan": args.kahan,
-                       "storage": "f32", "parallelism": f"replicas x{world}",
+                       "storage": "f32", "parallelism": f"replicas x{world}", "tiling": list(tiling),
                        "l2": "inputs larger than L2 (each resident grid > 129 MB)"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "gpu_launches": int(launches),
             "plain": plain, "check": {"misfit": misfit_val, "grad_l2": grad_norm, "k": float(kd.item())},
