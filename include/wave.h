@@ -173,9 +173,21 @@ wave_status wave_model_destroy(wave_model model);
 wave_status wave_model_set_block(wave_model model, int64_t zblock);
 wave_status wave_model_get_block(wave_model model, int64_t* zblock);
 /* Full tiling of the 3D FP32 step kernel: zblock as above, tile_rows (8 or 16
- * rows of 128 cells per CTA) and ring_depth (2 or 3 planes staged ahead in
- * the shared-memory ring).  Speed only; results are identical. */
-wave_status wave_model_set_tiling(wave_model model, int64_t zblock, int32_t tile_rows, int32_t ring_depth);
+ * rows of 128 cells per CTA), ring_depth (2 or 3 planes staged ahead in the
+ * shared-memory ring) and pipeline (0: per-thread cp.async copies with one
+ * CTA barrier per plane; 1: TMA bulk row copies issued by one warp, mbarrier
+ * full/empty handshakes, no CTA barrier per plane).  Speed only; results are
+ * identical. */
+wave_status wave_model_set_tiling(wave_model model, int64_t zblock, int32_t tile_rows, int32_t ring_depth,
+                                  int32_t pipeline);
+/* Waits for `stream` and reports whether a bounded device wait of the TMA
+ * pipeline gave up since the last check (WAVE_ETIMEOUT; the results of that
+ * call are invalid).  Clears the error word. */
+wave_status wave_model_check(wave_model model, void* stream);
+/* Test hook: stall_pipeline = 1 makes the TMA pipeline issue no copies, so
+ * its first wait runs out after wait_limit_cycles (default about 4e9 cycles);
+ * used to test the time-out path without a hang.  Not for production use. */
+wave_status wave_model_set_debug(wave_model model, int32_t stall_pipeline, int64_t wait_limit_cycles);
 
 /* ---- forward ---------------------------------------------------------------
  * Leapfrog u^{n+1} = 2u^n - u^{n-1} + dt^2/a (L u^n + f^n) for n = 1..N_s with

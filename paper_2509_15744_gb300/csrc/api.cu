@@ -76,6 +76,10 @@ struct wave_model_s {
   int64_t zblock;
   int tile_rows;     // 3D ring kernel: 8 or 16 rows per CTA
   int ring_depth;    // 3D ring kernel: 2 or 3 planes copied ahead
+  int pipeline;      // 3D FP32: 0 cp.async ring, 1 TMA bulk copies + mbarriers
+  int* err;          // device error word (bounded waits)
+  long long wait_limit_cycles;
+  int debug_stall;
   double stability;
 };
 
@@ -157,11 +161,12 @@ wave_status wave_wavelet(int32_t kind, double freq, int32_t nc, double psi0, dou
 // model
 // ---------------------------------------------------------------------------
 static void carve_model(Carve& c, const Geom& g, int physics, float** coef, float** bmat, float** part,
-                        float** maxv) {
+                        float** maxv, int** err) {
   *coef = c.take<float>(g.cells);
   *bmat = physics == WAVE_DENSITY ? c.take<float>(g.cells) : nullptr;
   *part = c.take<float>(1024);
   *maxv = c.take<float>(1);
+  *err = c.take<int>(1);
 }
 
 wave_status wave_model_workspace_size(const wave_grid_desc* desc, size_t* bytes) {
@@ -171,7 +176,8 @@ wave_status wave_model_workspace_size(const wave_grid_desc* desc, size_t* bytes)
   Geom g = make_geom(desc);
   Carve c(nullptr);
   float *a, *b, *p, *m;
-  carve_model(c, g, desc->physics, &a, &b, &p, &m);
+  int* e;
+  carve_model(c, g, desc->physics, &a, &b, &p, &m, &e);
   *bytes = c.off;
   return WAVE_OK;
 }
@@ -189,7 +195,9 @@ wave_status wave_model_create(const wave_grid_desc* desc, const float* param_dev
   Geom g = make_geom(desc);
   Carve c(workspace_dev);
   float *coef, *bmat, *part, *maxv;
-  carve_model(c, g, desc->physics, &coef, &bmat, &part, &maxv);
+  int* errw;
+  carve_model(c, g, desc->physics, &coef, &bmat, &part, &maxv, &errw);
+  CUDA_TRY(cudaMemsetAsync(errw, 0, sizeof(int), s));
   double sym;
   if (desc->physics == WAVE_VELOCITY) {
     CUDA_TRY(launch_coef_velocity(g, param_dev, (float)(desc->dt / desc->h), coef, s));
@@ -214,6 +222,10 @@ wave_status wave_model_create(const wave_grid_desc* desc, const float* param_dev
   m->zblock = default_zblock(g);
   m->tile_rows = 8;
   m->ring_depth = 3;
+  m->pipeline = 0;
+  m->err = errw;
+  m->wait_limit_cycles = 4000000000LL;  // about two seconds at the maximum SM clock
+  m->debug_stall = 0;
   m->stability = host_max;
   *out = m;
   return WAVE_OK;
@@ -237,13 +249,37 @@ wave_status wave_model_get_block(wave_model model, int64_t* zblock) {
   return WAVE_OK;
 }
 
-wave_status wave_model_set_tiling(wave_model model, int64_t zblock, int32_t tile_rows, int32_t ring_depth) {
+wave_status wave_model_set_tiling(wave_model model, int64_t zblock, int32_t tile_rows, int32_t ring_depth,
+                                  int32_t pipeline) {
   if (!model || zblock < 1) return WAVE_EINVAL;
   if (tile_rows != 8 && tile_rows != 16) return WAVE_EINVAL;
   if (ring_depth != 2 && ring_depth != 3) return WAVE_EINVAL;
+  if (pipeline != 0 && pipeline != 1) return WAVE_EINVAL;
   model->zblock = zblock;
   model->tile_rows = tile_rows;
   model->ring_depth = ring_depth;
+  model->pipeline = pipeline;
+  return WAVE_OK;
+}
+
+wave_status wave_model_check(wave_model model, void* stream) {
+  if (!model) return WAVE_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  int host = 0;
+  CUDA_TRY(cudaMemcpyAsync(&host, model->err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  if (host) {
+    CUDA_TRY(cudaMemsetAsync(model->err, 0, sizeof(int), s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    return WAVE_ETIMEOUT;
+  }
+  return WAVE_OK;
+}
+
+wave_status wave_model_set_debug(wave_model model, int32_t stall_pipeline, int64_t wait_limit_cycles) {
+  if (!model || wait_limit_cycles < 1) return WAVE_EINVAL;
+  model->debug_stall = stall_pipeline != 0;
+  model->wait_limit_cycles = wait_limit_cycles;
   return WAVE_OK;
 }
 
@@ -281,6 +317,10 @@ static StepArgs step_args(const wave_model_s* m, const void* cur, void* prev) {
   a.zblock = m->zblock;
   a.tile_rows = m->tile_rows;
   a.ring_depth = m->ring_depth;
+  a.pipeline = m->pipeline;
+  a.err = m->err;
+  a.wait_limit_cycles = m->wait_limit_cycles;
+  a.debug_stall = m->debug_stall;
   return a;
 }
 
@@ -752,6 +792,9 @@ static wave_status gradient_batched(wave_model m, const wave_shot* shots, int32_
     memset(&b, 0, sizeof(b));
     b.base = base;
     b.base.acc_scale = 1.f;
+    b.err = m->err;
+    b.wait_limit_cycles = m->wait_limit_cycles;
+    b.debug_stall = m->debug_stall;
     for (int si = 0; si < nshots; ++si) {
       if (shots[si].nt < n) continue;
       b.cur[b.nshots] = static_cast<const float*>(cur[si]);
@@ -826,6 +869,9 @@ static wave_status gradient_batched(wave_model m, const wave_shot* shots, int32_
     memset(&b, 0, sizeof(b));
     b.base = base;
     b.base.acc_scale = -1.f;
+    b.err = m->err;
+    b.wait_limit_cycles = m->wait_limit_cycles;
+    b.debug_stall = m->debug_stall;
     for (int si = 0; si < nshots; ++si) {
       if (shots[si].nt < t) continue;
       b.cur[b.nshots] = static_cast<const float*>(us_cur[si]);

@@ -266,6 +266,7 @@ static cudaError_t launch_ring_r(const BatchArgs& a, cudaStream_t s) {
 }
 
 cudaError_t launch_step3d_batched(const BatchArgs& b, int order, cudaStream_t s) {
+  if (b.base.pipeline == 1) return launch_step3d_tma(b, order, s);
   switch (order) {
     case 2: return launch_ring_r<1>(b, s);
     case 4: return launch_ring_r<2>(b, s);
@@ -282,6 +283,9 @@ cudaError_t launch_step3d_ring(const StepArgs& a, int order, cudaStream_t s) {
   b.cur[0] = reinterpret_cast<const float*>(a.u_cur);
   b.prev[0] = reinterpret_cast<float*>(a.u_prev);
   b.accf[0] = a.acc_mass;
+  b.err = a.err;
+  b.wait_limit_cycles = a.wait_limit_cycles;
+  b.debug_stall = a.debug_stall;
   return launch_step3d_batched(b, order, s);
 }
 

@@ -133,6 +133,10 @@ struct StepArgs {
   int64_t zblock;        // cells of the march axis per CTA (3D) / warp (2D)
   int tile_rows;         // 3D ring kernel: rows per CTA (8 or 16)
   int ring_depth;        // 3D ring kernel: planes copied ahead (2 or 3)
+  int pipeline;          // 3D FP32: 0 cp.async ring, 1 TMA bulk-copy pipeline
+  int* err;              // device error word (TMA pipeline)
+  long long wait_limit_cycles;
+  int debug_stall;
   // Exact (stored-history) mode, FP32 velocity only:
   void* u_out;           // output level (nullable: overwrite u_prev)
   const float* mix_a;    // stored u^j (nullable): accumulate the mixed term
@@ -153,8 +157,13 @@ struct BatchArgs {
   const float* cur[kMaxBatch];   // level n of each shot
   float* prev[kMaxBatch];        // level n-1 -> n+1 of each shot
   int accf[kMaxBatch];           // accumulate this shot's increment this step
+  // TMA pipeline only:
+  int* err;                      // set to 1 when a bounded wait gives up
+  long long wait_limit_cycles;   // bound of every wait (clock64 cycles)
+  int debug_stall;               // test only: issue no copies, so the first wait runs out
 };
 cudaError_t launch_step3d_batched(const BatchArgs& b, int order, cudaStream_t s);
+cudaError_t launch_step3d_tma(const BatchArgs& b, int order, cudaStream_t s);
 
 
 // ---- sparse (source / receiver) kernel -----------------------------------

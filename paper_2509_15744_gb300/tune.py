@@ -21,13 +21,14 @@ CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "tune_c
 
 def candidates(ndim: int, nz: int):
     if ndim == 2:
-        return [(zb, 8, 3) for zb in (8, 16, 32, 64, 128) if zb <= max(8, nz)]
+        return [(zb, 8, 3, 0) for zb in (8, 16, 32, 64, 128) if zb <= max(8, nz)]
     out = []
-    for rows in (8, 16):
-        for depth in (2, 3):
-            for zb in (16, 32, 64, 128):
-                if zb <= max(16, nz):
-                    out.append((zb, rows, depth))
+    for pipe in (0, 1):
+        for rows in (8, 16):
+            for depth in (2, 3):
+                for zb in (16, 32, 64, 128):
+                    if zb <= max(16, nz):
+                        out.append((zb, rows, depth, pipe))
     return out
 
 

@@ -74,7 +74,9 @@ _model_create = _sig("wave_model_create", _st, C.POINTER(GridDesc), _vp, _vp, _s
 _model_destroy = _sig("wave_model_destroy", _st, _vp)
 _model_set_block = _sig("wave_model_set_block", _st, _vp, C.c_int64)
 _model_get_block = _sig("wave_model_get_block", _st, _vp, C.POINTER(C.c_int64))
-_model_set_tiling = _sig("wave_model_set_tiling", _st, _vp, C.c_int64, _i32, _i32)
+_model_set_tiling = _sig("wave_model_set_tiling", _st, _vp, C.c_int64, _i32, _i32, _i32)
+_model_check = _sig("wave_model_check", _st, _vp, _vp)
+_model_set_debug = _sig("wave_model_set_debug", _st, _vp, _i32, C.c_int64)
 _fwd_ws = _sig("wave_forward_workspace_size", _st, _vp, C.POINTER(ShotDesc), _i32, C.POINTER(_sz))
 _forward = _sig("wave_forward", _st, _vp, C.POINTER(ShotDesc), _i32, _vp, _vp, _vp, _sz, _vp)
 _grad_ws = _sig("wave_gradient_workspace_size", _st, _vp, C.POINTER(ShotDesc), _i32, C.POINTER(GradOpts),
@@ -257,8 +259,16 @@ class Model:
     def set_block(self, zblock: int):
         _check(_model_set_block(self._h, int(zblock)), "wave_model_set_block")
 
-    def set_tiling(self, zblock: int, tile_rows: int = 8, ring_depth: int = 3):
-        _check(_model_set_tiling(self._h, int(zblock), int(tile_rows), int(ring_depth)), "wave_model_set_tiling")
+    def set_tiling(self, zblock: int, tile_rows: int = 8, ring_depth: int = 3, pipeline: int = 0):
+        _check(_model_set_tiling(self._h, int(zblock), int(tile_rows), int(ring_depth), int(pipeline)),
+               "wave_model_set_tiling")
+
+    def check(self, stream=None) -> int:
+        """Wait for the stream; WAVE_ETIMEOUT (5) if a bounded device wait gave up."""
+        return int(_model_check(self._h, _stream(stream)))
+
+    def set_debug(self, stall_pipeline: bool, wait_limit_cycles: int = 4_000_000_000):
+        _check(_model_set_debug(self._h, int(bool(stall_pipeline)), int(wait_limit_cycles)), "wave_model_set_debug")
 
     def get_block(self) -> int:
         v = C.c_int64(0)

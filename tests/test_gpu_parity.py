@@ -129,12 +129,14 @@ def test_3d_tilings_give_identical_results(W, order):
     shots = gpu_shots(W, prob, with_observed=False)
     base_tr, base_fin = m.forward(shots, return_final=True)
     g0, _, _ = m.gradient(gpu_shots(W, prob), k=2.0)
-    for zb, rows, depth in [(64, 8, 2), (64, 16, 3), (7, 16, 2), (5, 8, 3), (37, 16, 3), (1, 8, 2)]:
-        m.set_tiling(zb, rows, depth)
+    for zb, rows, depth, pipe in [(64, 8, 2, 0), (64, 16, 3, 0), (7, 16, 2, 0), (5, 8, 3, 0), (37, 16, 3, 0),
+                                  (1, 8, 2, 0), (64, 8, 3, 1), (16, 16, 2, 1), (5, 8, 2, 1), (37, 16, 3, 1),
+                                  (1, 8, 3, 1)]:
+        m.set_tiling(zb, rows, depth, pipe)
         tr, fin = m.forward(shots, return_final=True)
         g1, _, _ = m.gradient(gpu_shots(W, prob), k=2.0)
-        assert torch.equal(tr[0], base_tr[0]) and torch.equal(fin, base_fin), (zb, rows, depth)
-        assert torch.equal(g1, g0), (zb, rows, depth)
+        assert torch.equal(tr[0], base_tr[0]) and torch.equal(fin, base_fin), (zb, rows, depth, pipe)
+        assert torch.equal(g1, g0), (zb, rows, depth, pipe)
 
 
 @pytest.mark.parametrize("bc", ["dirichlet", "neumann"])
@@ -416,3 +418,39 @@ def test_exact_mode_param_gradient(W):
     med = prob.medium()
     _, g_ref, _ = O.exact_gradient(med, prob.oracle_shots(), prob.nt[0])
     assert rel_l2(gv.cpu().numpy(), med.param_chain(g_ref)) < GRAD_TOL
+
+
+@pytest.mark.parametrize("bc", ["dirichlet", "neumann"])
+def test_tma_pipeline_batched_matches_cp_async_ring(W, bc):
+    shape = (23, 21, 259)
+    prob = make_problem(shape, 8, bc, nshots=3, nt_list=[30, 22, 26], nrec=30, seed=61)
+    m = gpu_model(W, prob, kahan=True)
+    m.set_tiling(8, 8, 3, 0)
+    g0, c0, k0 = m.gradient(gpu_shots(W, prob), batched=True, k=2.5)
+    for zb, rows, depth in [(8, 8, 3), (16, 16, 2), (23, 8, 2)]:
+        m.set_tiling(zb, rows, depth, 1)
+        g1, c1, _ = m.gradient(gpu_shots(W, prob), batched=True, k=2.5)
+        torch.cuda.synchronize()
+        assert m.check() == 0
+        assert torch.equal(g1, g0), (zb, rows, depth)
+        assert float(c1.item()) == float(c0.item())
+
+
+def test_tma_pipeline_wait_times_out_without_hanging(W):
+    # Failure detection: a pipeline whose copies are never issued must give
+    # up after its bounded wait, report WAVE_ETIMEOUT and leave the context
+    # usable.
+    prob = make_problem((20, 17, 140), 4, "dirichlet", nt=6, nrec=10, seed=62)
+    m = gpu_model(W, prob)
+    m.set_tiling(8, 8, 3, 1)
+    ref, _, _ = m.gradient(gpu_shots(W, prob), k=1.0)
+    torch.cuda.synchronize()
+    assert m.check() == 0
+    m.set_debug(True, wait_limit_cycles=2_000_000)
+    m.forward(gpu_shots(W, prob, with_observed=False))
+    assert m.check() == 5
+    m.set_debug(False)
+    again, _, _ = m.gradient(gpu_shots(W, prob), k=1.0)
+    torch.cuda.synchronize()
+    assert m.check() == 0
+    assert torch.equal(again, ref)
