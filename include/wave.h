@@ -173,11 +173,11 @@ wave_status wave_model_destroy(wave_model model);
 wave_status wave_model_set_block(wave_model model, int64_t zblock);
 wave_status wave_model_get_block(wave_model model, int64_t* zblock);
 /* Full tiling of the 3D FP32 step kernel: zblock as above, tile_rows (8 or 16
- * rows of 128 cells per CTA), ring_depth (2 or 3 planes staged ahead in the
- * shared-memory ring) and pipeline (0: per-thread cp.async copies with one
- * CTA barrier per plane; 1: TMA bulk row copies issued by one warp, mbarrier
- * full/empty handshakes, no CTA barrier per plane).  Speed only; results are
- * identical. */
+ * rows of 128 cells per CTA), ring_depth (2 or 3 planes staged ahead in
+ * the shared-memory ring) and pipeline (0: per-thread cp.async copies with one
+ * CTA barrier per plane; 1: TMA bulk row copies, mbarrier full/empty
+ * handshakes, no CTA barrier per plane; 2: cp.async copies, two planes per
+ * CTA barrier, 8 rows only).  Speed only; results are identical. */
 wave_status wave_model_set_tiling(wave_model model, int64_t zblock, int32_t tile_rows, int32_t ring_depth,
                                   int32_t pipeline);
 /* Waits for `stream` and reports whether a bounded device wait of the TMA

@@ -254,7 +254,8 @@ wave_status wave_model_set_tiling(wave_model model, int64_t zblock, int32_t tile
   if (!model || zblock < 1) return WAVE_EINVAL;
   if (tile_rows != 8 && tile_rows != 16) return WAVE_EINVAL;
   if (ring_depth != 2 && ring_depth != 3) return WAVE_EINVAL;
-  if (pipeline != 0 && pipeline != 1) return WAVE_EINVAL;
+  if (pipeline < 0 || pipeline > 2) return WAVE_EINVAL;
+  if (pipeline == 2 && tile_rows != 8) return WAVE_EINVAL;
   model->zblock = zblock;
   model->tile_rows = tile_rows;
   model->ring_depth = ring_depth;

@@ -133,7 +133,7 @@ struct StepArgs {
   int64_t zblock;        // cells of the march axis per CTA (3D) / warp (2D)
   int tile_rows;         // 3D ring kernel: rows per CTA (8 or 16)
   int ring_depth;        // 3D ring kernel: planes copied ahead (2 or 3)
-  int pipeline;          // 3D FP32: 0 cp.async ring, 1 TMA bulk-copy pipeline
+  int pipeline;          // 3D FP32: 0 cp.async ring, 1 TMA bulk-copy pipeline, 2 cp.async ring with two planes per barrier
   int* err;              // device error word (TMA pipeline)
   long long wait_limit_cycles;
   int debug_stall;
@@ -164,6 +164,7 @@ struct BatchArgs {
 };
 cudaError_t launch_step3d_batched(const BatchArgs& b, int order, cudaStream_t s);
 cudaError_t launch_step3d_tma(const BatchArgs& b, int order, cudaStream_t s);
+cudaError_t launch_step3d_ring2(const BatchArgs& b, int order, cudaStream_t s);
 
 
 // ---- sparse (source / receiver) kernel -----------------------------------

@@ -131,7 +131,7 @@ def test_3d_tilings_give_identical_results(W, order):
     g0, _, _ = m.gradient(gpu_shots(W, prob), k=2.0)
     for zb, rows, depth, pipe in [(64, 8, 2, 0), (64, 16, 3, 0), (7, 16, 2, 0), (5, 8, 3, 0), (37, 16, 3, 0),
                                   (1, 8, 2, 0), (64, 8, 3, 1), (16, 16, 2, 1), (5, 8, 2, 1), (37, 16, 3, 1),
-                                  (1, 8, 3, 1)]:
+                                  (1, 8, 3, 1), (64, 8, 3, 2), (7, 8, 2, 2), (1, 8, 3, 2), (37, 8, 2, 2)]:
         m.set_tiling(zb, rows, depth, pipe)
         tr, fin = m.forward(shots, return_final=True)
         g1, _, _ = m.gradient(gpu_shots(W, prob), k=2.0)
@@ -427,8 +427,8 @@ def test_tma_pipeline_batched_matches_cp_async_ring(W, bc):
     m = gpu_model(W, prob, kahan=True)
     m.set_tiling(8, 8, 3, 0)
     g0, c0, k0 = m.gradient(gpu_shots(W, prob), batched=True, k=2.5)
-    for zb, rows, depth in [(8, 8, 3), (16, 16, 2), (23, 8, 2)]:
-        m.set_tiling(zb, rows, depth, 1)
+    for zb, rows, depth, pipe in [(8, 8, 3, 1), (16, 16, 2, 1), (23, 8, 2, 1), (8, 8, 3, 2), (23, 8, 2, 2)]:
+        m.set_tiling(zb, rows, depth, pipe)
         g1, c1, _ = m.gradient(gpu_shots(W, prob), batched=True, k=2.5)
         torch.cuda.synchronize()
         assert m.check() == 0
