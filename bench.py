@@ -40,6 +40,9 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="w2", choices=["w0", "w1", "w2", "w3", "w4"])
     ap.add_argument("--mode", default="auto", choices=["auto", "plain", "batched"])
+    ap.add_argument("--grad-mode", default="superposition", choices=["superposition", "symmetric", "reverse"],
+                    help="gradient: Algorithm 1, the +-k mean, or the two-field reverse-time adjoint "
+                         "(the last two are exact and run shot by shot)")
     ap.add_argument("--kahan", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -259,6 +262,8 @@ def main():
     dt = W.cfl_dt(wl.ndim, wl.order, wl.h, wl.vmax, wl.cfl_fraction)
     batched_ok = wl.ndim == 3 and wl.physics == "velocity" and wl.nshots > 1
     mode = args.mode if args.mode != "auto" else ("batched" if batched_ok else "plain")
+    if args.grad_mode != "superposition":
+        mode = "plain"
 
     def barrier():
         torch.cuda.synchronize()
@@ -280,7 +285,7 @@ def main():
         del mtrue, ptrue
     shots = [W.Shot(wl.sources[i], wavs[i], recs[i], observed[i]) for i in range(wl.nshots)]
     model = W.Model(param0, wl.h, dt, wl.order, wl.physics, wl.bc, kahan=args.kahan)
-    gkw = dict(objective=wl.objective, patch_sign=wl.patch_sign, batched=(mode == "batched"))
+    gkw = dict(objective=wl.objective, patch_sign=wl.patch_sign, batched=(mode == "batched"), mode=args.grad_mode)
     from paper_2509_15744_gb300 import tune
     tiling = tune.tune(model, shots, batched=(mode == "batched"))
 
@@ -384,7 +389,8 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": wl.name, "shape": list(wl.shape), "order": wl.order, "physics": wl.physics,
-                       "shots": wl.nshots, "nt_total": int(sum(wl.nt)), "mode": mode, "kahan": args.kahan,
+                       "shots": wl.nshots, "nt_total": int(sum(wl.nt)), "mode": mode,
+                       "gradient": args.grad_mode, "kahan": args.kahan,
                        "storage": "f32", "parallelism": f"replicas x{world}", "tiling": list(tiling),
                        "l2": "inputs larger than L2 (each resident grid > 129 MB)"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "gpu_launches": int(launches),

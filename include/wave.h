@@ -73,7 +73,13 @@ typedef enum {
 
 typedef enum {
   WAVE_SUPERPOSITION = 0, /* Algorithm 1: K~ = (K(u^s,u^s) - K(u,u)) / 2k, memory independent of N */
-  WAVE_EXACT_STORED = 1   /* standard adjoint over the stored forward history (comparator; memory ~ N grids) */
+  WAVE_EXACT_STORED = 1,  /* standard adjoint over the stored forward history (comparator; memory ~ N grids) */
+  WAVE_SYMMETRIC_K = 2,   /* (K~(k) + K~(-k)) / 2 = (K(u^+,u^+) - K(u^-,u^-)) / 4k, u^+- = u +- k u_adj:
+                             two superposed fields from one forward; the k^2 term of Eq. superposedkernel1
+                             cancels, so the result is the exact discrete gradient (2 more grids) */
+  WAVE_EXACT_REVERSE = 3  /* exact gradient without history: u reconstructed backward by time reversal
+                             (leapfrog is reversible) beside the adjoint field, accumulating the mixed term
+                             of Eq. kernel1 directly (velocity form, FP32 storage; 2 more grids) */
 } wave_grad_mode;
 
 typedef enum {
@@ -119,7 +125,8 @@ typedef struct {
   int32_t grad_wrt;    /* wave_grad_wrt */
   double patch_sign;   /* +1 suppress / -1 amplify (Sec. 5.2 sign flip); patch objective only */
   double k;            /* superposition factor (Eq. superposedforce); <= 0 selects it automatically */
-  double k_ratio;      /* automatic k = k_ratio * ||psi|| / ||f_adj|| of the first shot; 0 -> 1e-2 */
+  double k_ratio;      /* automatic k = k_ratio * ||psi|| / ||f_adj|| of the first shot;
+                          0 -> 1e-2 (WAVE_SUPERPOSITION) or 1 (WAVE_SYMMETRIC_K, which has no k^2 gap) */
 } wave_gradient_opts;
 
 typedef struct wave_model_s* wave_model;
@@ -210,7 +217,16 @@ wave_status wave_forward(wave_model model, const wave_shot* shots, int32_t nshot
  * misfit_dev: one double, C summed over shots.  k_dev: one double, the k used
  * (all shots share it).  Exact mode (velocity form, FP32 storage, one shot at
  * a time) stores the forward history u^0..u^{N+1} instead and returns the
- * standard adjoint gradient; k_dev then receives 0. */
+ * standard adjoint gradient; k_dev then receives 0.
+ * WAVE_SYMMETRIC_K: the forward accumulates nothing; two superposed fields
+ * with +k and -k run backward from copies of (u^{N+1}, u^N), accumulating
+ * -K(u^+,u^+) and +K(u^-,u^-); the result is divided by 4k.  In 3D velocity
+ * form with FP32 storage both fields advance in one launch (coef and the
+ * accumulator are read once per step).
+ * WAVE_EXACT_REVERSE: per backward step j, u^{j-1} = 2u^j - u^{j+1} + dt^2/m
+ * (L u^j + f^j) and the adjoint lambda^{j-1} from lambda^{N+1} = lambda^N = 0
+ * with the adjoint source alone, accumulating -(lambda^j - lambda^{j-1})
+ * (u^j - u^{j-1}); k_dev receives 0.  Neither new mode supports batched = 1. */
 wave_status wave_gradient_workspace_size(wave_model model, const wave_shot* shots, int32_t nshots,
                                          const wave_gradient_opts* opts, size_t* bytes);
 wave_status wave_adjoint_sensitivity(wave_model model, const wave_shot* shots, int32_t nshots,

@@ -509,3 +509,19 @@ def superposition_gradient(med: Medium, shots: Sequence[Shot], nt: int, k: float
                 k_s += med.kernel_level(us, us)
             us_next, us = us, us_prev
     return dict(C=total_c, K_tilde=(k_s - k_f) / (2.0 * k), K_f=k_f, K_s=k_s)
+
+
+def symmetric_superposition_gradient(med: Medium, shots: Sequence[Shot], nt: int, k: float):
+    """Mean of the superposition result at +k and -k.
+
+    K_tilde(k) = g + (k/2) K(u_adj, u_adj) (Eq. superposedkernel1 applied to
+    the discrete bilinear kernel) is affine in k, so the mean over +-k drops
+    the k^2 term and equals the exact gradient g; the forward kernel K(u, u)
+    cancels as well, leaving (K(u^+,u^+) - K(u^-,u^-)) / 4k with
+    u^+- = u +- k u_adj.
+
+    Returns dict(C, K_tilde).
+    """
+    plus = superposition_gradient(med, shots, nt, k)
+    minus = superposition_gradient(med, shots, nt, -k)
+    return dict(C=plus["C"], K_tilde=0.5 * (plus["K_tilde"] + minus["K_tilde"]))

@@ -531,13 +531,16 @@ struct GradWs {
   float* comp;
   void* u0;
   void* u1;
+  void* u2;  // second field pair (WAVE_SYMMETRIC_K: u^-; WAVE_EXACT_REVERSE: lambda), else null
+  void* u3;
   float* resid;
   int64_t* recp;
   double* parts;
   double* scal;  // [0] k, [1] psi2, [2] e2
 };
 
-static void carve_gradient(Carve& c, const wave_model_s* m, const wave_shot* shots, int32_t nshots, GradWs* w) {
+static void carve_gradient(Carve& c, const wave_model_s* m, const wave_shot* shots, int32_t nshots, int mode,
+                           GradWs* w) {
   int64_t maxres = 1;
   int32_t maxrec = 1;
   for (int s = 0; s < nshots; ++s) {
@@ -549,6 +552,9 @@ static void carve_gradient(Carve& c, const wave_model_s* m, const wave_shot* sho
   w->comp = m->d.kahan ? c.take<float>(m->g.cells) : nullptr;
   w->u0 = c.take_bytes(m->g.cells * eb);
   w->u1 = c.take_bytes(m->g.cells * eb);
+  const bool two = mode == WAVE_SYMMETRIC_K || mode == WAVE_EXACT_REVERSE;
+  w->u2 = two ? c.take_bytes(m->g.cells * eb) : nullptr;
+  w->u3 = two ? c.take_bytes(m->g.cells * eb) : nullptr;
   w->resid = c.take<float>(maxres);
   w->recp = c.take<int64_t>(maxrec);
   w->parts = c.take<double>(1024);
@@ -558,11 +564,12 @@ static void carve_gradient(Carve& c, const wave_model_s* m, const wave_shot* sho
 static wave_status validate_opts(const wave_model_s* m, const wave_gradient_opts* o) {
   if (!o) return WAVE_EINVAL;
   if (o->objective != WAVE_OBJ_L2 && o->objective != WAVE_OBJ_PATCH) return WAVE_EINVAL;
-  if (o->mode != WAVE_SUPERPOSITION && o->mode != WAVE_EXACT_STORED) return WAVE_EINVAL;
+  if (o->mode < WAVE_SUPERPOSITION || o->mode > WAVE_EXACT_REVERSE) return WAVE_EINVAL;
   if (o->grad_wrt != WAVE_GRAD_MASS && o->grad_wrt != WAVE_GRAD_PARAM) return WAVE_EINVAL;
-  if (o->mode == WAVE_EXACT_STORED &&
+  if ((o->mode == WAVE_EXACT_STORED || o->mode == WAVE_EXACT_REVERSE) &&
       (o->batched || m->d.physics != WAVE_VELOCITY || m->d.storage != WAVE_F32))
     return WAVE_EUNSUPPORTED;
+  if (o->mode == WAVE_SYMMETRIC_K && o->batched) return WAVE_EUNSUPPORTED;
   if (o->batched && !(m->d.ndim == 3 && m->d.physics == WAVE_VELOCITY && m->d.storage == WAVE_F32))
     return WAVE_EUNSUPPORTED;
   return WAVE_OK;
@@ -648,7 +655,7 @@ extern "C" wave_status wave_gradient_workspace_size(wave_model m, const wave_sho
     carve_batched(c, m, shots, nshots, &w);
   } else {
     GradWs w;
-    carve_gradient(c, m, shots, nshots, &w);
+    carve_gradient(c, m, shots, nshots, opts->mode, &w);
   }
   *bytes = c.off;
   return WAVE_OK;
@@ -917,16 +924,21 @@ extern "C" wave_status wave_adjoint_sensitivity(wave_model m, const wave_shot* s
   const double dt = m->d.dt;
   Carve c(ws);
   GradWs w;
-  carve_gradient(c, m, shots, nshots, &w);
+  carve_gradient(c, m, shots, nshots, opts->mode, &w);
   double* kd = w.scal + 0;
   double* misfit_acc = misfit_dev ? misfit_dev : w.scal + 3;
+  const bool sym = opts->mode == WAVE_SYMMETRIC_K;
+  const bool rev = opts->mode == WAVE_EXACT_REVERSE;
 
   CUDA_TRY(cudaMemsetAsync(w.acc, 0, g.cells * sizeof(float), s));
   if (w.comp) CUDA_TRY(cudaMemsetAsync(w.comp, 0, g.cells * sizeof(float), s));
   CUDA_TRY(cudaMemsetAsync(misfit_acc, 0, sizeof(double), s));
-  const bool auto_k = !(opts->k > 0.0);
-  if (!auto_k) CUDA_TRY(launch_set_k(kd, opts->k, s));
-  const double ratio = opts->k_ratio > 0.0 ? opts->k_ratio : 1e-2;
+  const bool auto_k = !rev && !(opts->k > 0.0);
+  if (rev) CUDA_TRY(launch_set_k(kd, 1.0, s));  // the adjoint source enters unscaled
+  else if (!auto_k) CUDA_TRY(launch_set_k(kd, opts->k, s));
+  const double ratio = opts->k_ratio > 0.0 ? opts->k_ratio : (sym ? 1.0 : 1e-2);
+  // both fields of WAVE_SYMMETRIC_K advance in one launch where the batched kernel applies
+  const bool fuse2 = sym && m->d.ndim == 3 && m->d.physics == WAVE_VELOCITY && stor == WAVE_F32;
 
   for (int si = 0; si < nshots; ++si) {
     const wave_shot& sh = shots[si];
@@ -958,8 +970,8 @@ extern "C" wave_status wave_adjoint_sensitivity(wave_model m, const wave_shot* s
       a.acc = w.acc;
       a.comp = w.comp;
       a.acc_scale = 1.f;
-      a.acc_mass = n <= N - 1;
-      a.acc_stiff = n <= N - 1;
+      a.acc_mass = !(sym || rev) && n <= N - 1;   // the two-field modes need no K(u,u)
+      a.acc_stiff = !(sym || rev) && n <= N - 1;
       CUDA_TRY(run_step(m, a, s));
       std::swap(prev, cur);  // cur = u^{n+1}
       if (n + 1 <= N) {
@@ -991,8 +1003,96 @@ extern "C" wave_status wave_adjoint_sensitivity(wave_model m, const wave_shot* s
       }
       CUDA_TRY(launch_auto_k(w.scal + 1, w.scal + 2, ratio, wgt, kd, s));
     }
-    // ---- superposed pass: u^s from (u^{N+1}, u^N), +K(u^s,u^s) ----------
     // prev holds u^N, cur holds u^{N+1}
+    if (rev) {
+      // ---- u backward by time reversal beside lambda (Eq. kernel1 mixed term)
+      CUDA_TRY(cudaMemsetAsync(w.u2, 0, g.cells * eb, s));
+      CUDA_TRY(cudaMemsetAsync(w.u3, 0, g.cells * eb, s));
+      void* u_c = prev;   // u^j
+      void* u_n = cur;    // u^{j+1}, overwritten with u^{j-1}
+      void* l_c = w.u3;   // lambda^j
+      void* l_n = w.u2;   // lambda^{j+1}, overwritten with lambda^{j-1}
+      SparseArgs fs = sparse_args(m, w.recp, 0);
+      fs.src_p = pitched_cell(g, sh.src_cell);
+      fs.wavelet = sh.wavelet_dev;
+      SparseArgs adj = sparse_args(m, w.recp, sh.nrec);
+      adj.resid_in = w.resid;
+      adj.k_dev = kd;
+      adj.weight = (float)wgt;
+      for (int j = N; j >= 1; --j) {
+        fs.dst = u_n;
+        fs.ilevel = j;
+        CUDA_TRY(launch_sparse(fs, stor, s));
+        CUDA_TRY(run_step(m, step_args(m, u_c, u_n), s));
+        adj.dst = l_n;
+        adj.ilevel = j;
+        CUDA_TRY(launch_sparse(adj, stor, s));
+        StepArgs a = step_args(m, l_c, l_n);
+        a.acc = w.acc;
+        a.acc_scale = -1.f;
+        a.acc_mass = 1;
+        a.mix_a = static_cast<const float*>(u_c);
+        a.mix_b = static_cast<const float*>(u_n);
+        CUDA_TRY(run_step(m, a, s));
+        std::swap(u_c, u_n);
+        std::swap(l_c, l_n);
+      }
+      continue;
+    }
+    if (sym) {
+      // ---- u^+ (k) on (prev, cur), u^- (-k) on copies of them ---------
+      CUDA_TRY(cudaMemcpyAsync(w.u2, prev, g.cells * eb, cudaMemcpyDeviceToDevice, s));
+      CUDA_TRY(cudaMemcpyAsync(w.u3, cur, g.cells * eb, cudaMemcpyDeviceToDevice, s));
+      void* fc[2] = {prev, w.u2};   // u^{+-,j}
+      void* fn[2] = {cur, w.u3};    // u^{+-,j+1}, overwritten with u^{+-,j-1}
+      SparseArgs sf[2];
+      for (int f = 0; f < 2; ++f) {
+        sf[f] = sparse_args(m, w.recp, sh.nrec);
+        sf[f].src_p = pitched_cell(g, sh.src_cell);
+        sf[f].wavelet = sh.wavelet_dev;
+        sf[f].resid_in = w.resid;
+        sf[f].k_dev = kd;
+        sf[f].weight = (float)(f == 0 ? wgt : -wgt);   // force f +- k f_adj
+      }
+      for (int j = N; j >= 1; --j) {
+        for (int f = 0; f < 2; ++f) {
+          sf[f].dst = fn[f];
+          sf[f].ilevel = j;
+          CUDA_TRY(launch_sparse(sf[f], stor, s));
+        }
+        if (fuse2) {
+          BatchArgs b;
+          memset(&b, 0, sizeof(b));
+          b.base = step_args(m, nullptr, nullptr);
+          b.base.acc = w.acc;
+          b.base.comp = w.comp;
+          b.base.acc_scale = -1.f;
+          b.err = m->err;
+          b.wait_limit_cycles = m->wait_limit_cycles;
+          b.debug_stall = m->debug_stall;
+          b.nshots = 2;
+          for (int f = 0; f < 2; ++f) {
+            b.cur[f] = static_cast<const float*>(fc[f]);
+            b.prev[f] = static_cast<float*>(fn[f]);
+            b.accf[f] = f == 0 ? 1.f : -1.f;   // -K(u^+,u^+) ... +K(u^-,u^-)
+          }
+          CUDA_TRY(run_batched(m, b, s));
+        } else {
+          for (int f = 0; f < 2; ++f) {
+            StepArgs a = step_args(m, fc[f], fn[f]);
+            a.acc = w.acc;
+            a.comp = w.comp;
+            a.acc_scale = f == 0 ? -1.f : 1.f;
+            a.acc_mass = 1;
+            a.acc_stiff = j <= N - 1;
+            CUDA_TRY(run_step(m, a, s));
+          }
+        }
+        for (int f = 0; f < 2; ++f) std::swap(fc[f], fn[f]);
+      }
+      continue;
+    }
+    // ---- superposed pass: u^s from (u^{N+1}, u^N), +K(u^s,u^s) ----------
     void* us_cur = prev;   // u^{s,j}
     void* us_next = cur;   // u^{s,j+1}, overwritten with u^{s,j-1}
     SparseArgs sb = sparse_args(m, w.recp, sh.nrec);
@@ -1015,10 +1115,12 @@ extern "C" wave_status wave_adjoint_sensitivity(wave_model m, const wave_shot* s
       std::swap(us_cur, us_next);  // us_cur = u^{s,j-1}, us_next = u^{s,j}
     }
   }
-  // ---- K~ = (K(u^s,u^s) - K(u,u)) / 2k (Eq. superposedkernel) ------------
-  CUDA_TRY(launch_finish(g, w.acc, kd, 1.0 / dt, 1, opts->grad_wrt == WAVE_GRAD_PARAM && m->d.physics == WAVE_VELOCITY,
-                         m->param, grad_dev, s));
-  if (k_dev) CUDA_TRY(cudaMemcpyAsync(k_dev, kd, sizeof(double), cudaMemcpyDeviceToDevice, s));
+  // ---- K~ = (K(u^s,u^s) - K(u,u)) / 2k (Eq. superposedkernel); the
+  // symmetric pair divides by 4k, the reverse-time mode by nothing ----------
+  const bool chain_v = opts->grad_wrt == WAVE_GRAD_PARAM && m->d.physics == WAVE_VELOCITY;
+  CUDA_TRY(launch_finish(g, w.acc, kd, (sym ? 0.5 : 1.0) / dt, rev ? 0 : 1, chain_v, m->param, grad_dev, s));
+  if (k_dev && rev) CUDA_TRY(cudaMemsetAsync(k_dev, 0, sizeof(double), s));
+  else if (k_dev) CUDA_TRY(cudaMemcpyAsync(k_dev, kd, sizeof(double), cudaMemcpyDeviceToDevice, s));
   return WAVE_OK;
 }
 

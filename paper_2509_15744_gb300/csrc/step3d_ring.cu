@@ -98,6 +98,7 @@ step3d_velocity_ring_kernel(BatchArgs b) {
     const float* __restrict__ uc = b.cur[shot];
     float* __restrict__ up = b.prev[shot];
     const bool acc_on = b.accf[shot] != 0;
+    const float acc_sc = a.acc_scale * b.accf[shot];  // per-shot sign and on/off
     // Stage plane p into ring slot `slot`; always commits one group.
     auto issue = [&](int p, int slot) {
       if (p < z1 + R) {
@@ -207,24 +208,24 @@ step3d_velocity_ring_kernel(BatchArgs b) {
         if (a.mix_a) {  // exact mode (one shot): acc += acc_scale (u_cur - u_next)(mix_a - mix_b)
           const float4 ma = *reinterpret_cast<const float4*>(a.mix_a + off);
           const float4 mb = *reinterpret_cast<const float4*>(a.mix_b + off);
-          ac.x = fmaf(a.acc_scale * (u.x - un.x), ma.x - mb.x, ac.x);
-          ac.y = fmaf(a.acc_scale * (u.y - un.y), ma.y - mb.y, ac.y);
-          ac.z = fmaf(a.acc_scale * (u.z - un.z), ma.z - mb.z, ac.z);
-          ac.w = fmaf(a.acc_scale * (u.w - un.w), ma.w - mb.w, ac.w);
+          ac.x = fmaf(acc_sc * (u.x - un.x), ma.x - mb.x, ac.x);
+          ac.y = fmaf(acc_sc * (u.y - un.y), ma.y - mb.y, ac.y);
+          ac.z = fmaf(acc_sc * (u.z - un.z), ma.z - mb.z, ac.z);
+          ac.w = fmaf(acc_sc * (u.w - un.w), ma.w - mb.w, ac.w);
           *reinterpret_cast<float4*>(a.acc + off) = ac;
         } else if (acc_on) {
           const float d0 = un.x - u.x, d1 = un.y - u.y, d2 = un.z - u.z, d3 = un.w - u.w;
           if (a.comp) {
-            kahan_add(ac.x, cp.x, a.acc_scale * d0 * d0);
-            kahan_add(ac.y, cp.y, a.acc_scale * d1 * d1);
-            kahan_add(ac.z, cp.z, a.acc_scale * d2 * d2);
-            kahan_add(ac.w, cp.w, a.acc_scale * d3 * d3);
+            kahan_add(ac.x, cp.x, acc_sc * d0 * d0);
+            kahan_add(ac.y, cp.y, acc_sc * d1 * d1);
+            kahan_add(ac.z, cp.z, acc_sc * d2 * d2);
+            kahan_add(ac.w, cp.w, acc_sc * d3 * d3);
             *reinterpret_cast<float4*>(a.comp + off) = cp;
           } else {
-            ac.x = fmaf(a.acc_scale * d0, d0, ac.x);
-            ac.y = fmaf(a.acc_scale * d1, d1, ac.y);
-            ac.z = fmaf(a.acc_scale * d2, d2, ac.z);
-            ac.w = fmaf(a.acc_scale * d3, d3, ac.w);
+            ac.x = fmaf(acc_sc * d0, d0, ac.x);
+            ac.y = fmaf(acc_sc * d1, d1, ac.y);
+            ac.z = fmaf(acc_sc * d2, d2, ac.z);
+            ac.w = fmaf(acc_sc * d3, d3, ac.w);
           }
           *reinterpret_cast<float4*>(a.acc + off) = ac;
         }

@@ -89,6 +89,7 @@ step3d_velocity_ring2_kernel(BatchArgs b) {
     const float* __restrict__ uc = b.cur[shot];
     float* __restrict__ up = b.prev[shot];
     const bool acc_on = b.accf[shot] != 0;
+    const float acc_sc = a.acc_scale * b.accf[shot];  // per-shot sign and on/off
 
     auto issue = [&](int p, int slot) {
       if (p < z1 + R) {
@@ -194,21 +195,21 @@ step3d_velocity_ring2_kernel(BatchArgs b) {
       if (a.mix_a) {
         const float4 ma = *reinterpret_cast<const float4*>(a.mix_a + off);
         const float4 mb = *reinterpret_cast<const float4*>(a.mix_b + off);
-        ac.x = fmaf(a.acc_scale * (u.x - un.x), ma.x - mb.x, ac.x);
-        ac.y = fmaf(a.acc_scale * (u.y - un.y), ma.y - mb.y, ac.y);
-        ac.z = fmaf(a.acc_scale * (u.z - un.z), ma.z - mb.z, ac.z);
-        ac.w = fmaf(a.acc_scale * (u.w - un.w), ma.w - mb.w, ac.w);
+        ac.x = fmaf(acc_sc * (u.x - un.x), ma.x - mb.x, ac.x);
+        ac.y = fmaf(acc_sc * (u.y - un.y), ma.y - mb.y, ac.y);
+        ac.z = fmaf(acc_sc * (u.z - un.z), ma.z - mb.z, ac.z);
+        ac.w = fmaf(acc_sc * (u.w - un.w), ma.w - mb.w, ac.w);
         *reinterpret_cast<float4*>(a.acc + off) = ac;
       } else if (acc_on) {
         const float d0 = un.x - u.x, d1 = un.y - u.y, d2 = un.z - u.z, d3 = un.w - u.w;
         if (a.comp) {
-          kahan_add(ac.x, cp.x, a.acc_scale * d0 * d0);
-          kahan_add(ac.y, cp.y, a.acc_scale * d1 * d1);
-          kahan_add(ac.z, cp.z, a.acc_scale * d2 * d2);
-          kahan_add(ac.w, cp.w, a.acc_scale * d3 * d3);
+          kahan_add(ac.x, cp.x, acc_sc * d0 * d0);
+          kahan_add(ac.y, cp.y, acc_sc * d1 * d1);
+          kahan_add(ac.z, cp.z, acc_sc * d2 * d2);
+          kahan_add(ac.w, cp.w, acc_sc * d3 * d3);
           *reinterpret_cast<float4*>(a.comp + off) = cp;
         } else {
-          const float2 sc = make_float2(a.acc_scale, a.acc_scale);
+          const float2 sc = make_float2(acc_sc, acc_sc);
           const float2 e01 = make_float2(d0, d1), e23 = make_float2(d2, d3);
           const float2 r01 = __ffma2_rn(__fmul2_rn(sc, e01), e01, make_float2(ac.x, ac.y));
           const float2 r23 = __ffma2_rn(__fmul2_rn(sc, e23), e23, make_float2(ac.z, ac.w));

@@ -192,6 +192,7 @@ step3d_velocity_tma_kernel(BatchArgs b) {
   for (int s = 0; s < b.nshots && ok; ++s) {
     float* __restrict__ up = b.prev[s];
     const bool acc_on = b.accf[s] != 0;
+    const float acc_sc = a.acc_scale * b.accf[s];  // per-shot sign and on/off
     const int base = s * per_shot;  // load index of plane z0-R of this shot
     float4 u_old = make_float4(0.f, 0.f, 0.f, 0.f), cf = u_old, ac = u_old, cp = u_old;
     auto load_streams = [&](int z, float4& uo, float4& c, float4& acv, float4& cpv) {
@@ -282,24 +283,24 @@ step3d_velocity_tma_kernel(BatchArgs b) {
         if (a.mix_a) {
           const float4 ma = *reinterpret_cast<const float4*>(a.mix_a + off);
           const float4 mb = *reinterpret_cast<const float4*>(a.mix_b + off);
-          ac.x = fmaf(a.acc_scale * (u.x - un.x), ma.x - mb.x, ac.x);
-          ac.y = fmaf(a.acc_scale * (u.y - un.y), ma.y - mb.y, ac.y);
-          ac.z = fmaf(a.acc_scale * (u.z - un.z), ma.z - mb.z, ac.z);
-          ac.w = fmaf(a.acc_scale * (u.w - un.w), ma.w - mb.w, ac.w);
+          ac.x = fmaf(acc_sc * (u.x - un.x), ma.x - mb.x, ac.x);
+          ac.y = fmaf(acc_sc * (u.y - un.y), ma.y - mb.y, ac.y);
+          ac.z = fmaf(acc_sc * (u.z - un.z), ma.z - mb.z, ac.z);
+          ac.w = fmaf(acc_sc * (u.w - un.w), ma.w - mb.w, ac.w);
           *reinterpret_cast<float4*>(a.acc + off) = ac;
         } else if (acc_on) {
           const float d0 = un.x - u.x, d1 = un.y - u.y, d2 = un.z - u.z, d3 = un.w - u.w;
           if (a.comp) {
-            kahan_add(ac.x, cp.x, a.acc_scale * d0 * d0);
-            kahan_add(ac.y, cp.y, a.acc_scale * d1 * d1);
-            kahan_add(ac.z, cp.z, a.acc_scale * d2 * d2);
-            kahan_add(ac.w, cp.w, a.acc_scale * d3 * d3);
+            kahan_add(ac.x, cp.x, acc_sc * d0 * d0);
+            kahan_add(ac.y, cp.y, acc_sc * d1 * d1);
+            kahan_add(ac.z, cp.z, acc_sc * d2 * d2);
+            kahan_add(ac.w, cp.w, acc_sc * d3 * d3);
             *reinterpret_cast<float4*>(a.comp + off) = cp;
           } else {
-            ac.x = fmaf(a.acc_scale * d0, d0, ac.x);
-            ac.y = fmaf(a.acc_scale * d1, d1, ac.y);
-            ac.z = fmaf(a.acc_scale * d2, d2, ac.z);
-            ac.w = fmaf(a.acc_scale * d3, d3, ac.w);
+            ac.x = fmaf(acc_sc * d0, d0, ac.x);
+            ac.y = fmaf(acc_sc * d1, d1, ac.y);
+            ac.z = fmaf(acc_sc * d2, d2, ac.z);
+            ac.w = fmaf(acc_sc * d3, d3, ac.w);
           }
           *reinterpret_cast<float4*>(a.acc + off) = ac;
         }

@@ -156,7 +156,7 @@ struct BatchArgs {
   int nshots;
   const float* cur[kMaxBatch];   // level n of each shot
   float* prev[kMaxBatch];        // level n-1 -> n+1 of each shot
-  int accf[kMaxBatch];           // accumulate this shot's increment this step
+  float accf[kMaxBatch];         // per-shot factor on acc_scale this step (0: no increment)
   // TMA pipeline only:
   int* err;                      // set to 1 when a bounded wait gives up
   long long wait_limit_cycles;   // bound of every wait (clock64 cycles)

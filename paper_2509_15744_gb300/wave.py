@@ -30,7 +30,7 @@ PHYSICS = {"velocity": 0, "density": 1}
 BC = {"dirichlet": 0, "neumann": 1}
 STORAGE = {"f32": 0, "bf16": 1, "f16": 2}
 OBJECTIVE = {"l2": 0, "patch": 1}
-MODE = {"superposition": 0, "exact": 1}
+MODE = {"superposition": 0, "exact": 1, "symmetric": 2, "reverse": 3}
 GRAD_WRT = {"mass": 0, "param": 1}
 WAVELET = {"ricker": 0, "sine_burst": 1}
 
@@ -304,7 +304,12 @@ class Model:
     def gradient(self, shots: Sequence[Shot], objective: str = "l2", k: Optional[float] = None,
                  k_ratio: Optional[float] = None, mode: str = "superposition", batched: bool = False,
                  grad_wrt: str = "mass", patch_sign: float = 1.0, stream=None, out: Optional[torch.Tensor] = None):
-        """Algorithm 1.  Returns (grad [*shape] float32, misfit [1] float64, k [1] float64)."""
+        """Algorithm 1.  Returns (grad [*shape] float32, misfit [1] float64, k [1] float64).
+
+        mode: "superposition" (Algorithm 1), "exact" (adjoint over the stored
+        forward history), "symmetric" (mean of the +k and -k superposition
+        results: exact, two more grids) or "reverse" (u reconstructed backward
+        beside the adjoint field: exact, two more grids, k returned as 0)."""
         dev = self.param.device
         o = GradOpts()
         o.objective, o.mode, o.batched, o.grad_wrt = OBJECTIVE[objective], MODE[mode], int(bool(batched)), \

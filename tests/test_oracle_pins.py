@@ -352,10 +352,11 @@ def test_superposition_identity(physics, order, bc, shape, objective):
     # the approximation error is the k/2 K(lam, lam) term, small for this k
     gap = np.linalg.norm(sup["K_tilde"] - g) / np.linalg.norm(g)
     assert gap < 0.05
-    # symmetric +-k average cancels the k^2 term exactly
-    sup_m = O.superposition_gradient(med, [p["shot"]], p["nt"], -k)
-    avg = 0.5 * (sup["K_tilde"] + sup_m["K_tilde"])
-    assert np.abs(avg - g).max() < 1e-7 * scale
+    # symmetric +-k average cancels the k^2 term exactly, at any k
+    for kk in (k, 30 * k):
+        sym = O.symmetric_superposition_gradient(med, [p["shot"]], p["nt"], kk)
+        assert abs(sym["C"] - c_ex) < 1e-12 * abs(c_ex)
+        assert np.abs(sym["K_tilde"] - g).max() < 1e-7 * scale
     # K_tilde is affine in k
     sup2 = O.superposition_gradient(med, [p["shot"]], p["nt"], 2 * k)
     np.testing.assert_allclose(sup2["K_tilde"] - sup["K_tilde"], 0.5 * k * klam, atol=1e-7 * scale)
