@@ -196,6 +196,28 @@ wave_status wave_model_check(wave_model model, void* stream);
  * used to test the time-out path without a hang.  Not for production use. */
 wave_status wave_model_set_debug(wave_model model, int32_t stall_pipeline, int64_t wait_limit_cycles);
 
+/* Row pitch (cells) of the model's resident grids: nx rounded up to 128.
+ * A pitched grid is [nz][ny][pitch] FP32 (or 16-bit storage), padding zero. */
+wave_status wave_model_pitch(wave_model model, int64_t* pitch);
+
+/* ---- one step ----------------------------------------------------------------
+ * One leapfrog step (Eq. FDstencil1 / FDstencil2 without force) of nfields
+ * independent fields on this model, in the launch configuration of the
+ * batched gradient (3D velocity form, FP32 storage: all fields in one launch;
+ * otherwise one launch per field):
+ *   prev_dev[f] <- 2 cur_dev[f] - prev_dev[f] + dt^2/a L cur_dev[f]
+ * and, if acc_dev is not NULL, the sensitivity increment of Algorithm 1 for
+ * that step: acc += acc_sign[f] * (u^{n+1} - u^n)^2 (density form: da times
+ * that minus dbs times the face-weighted squared differences of u^n), with
+ * Kahan compensation in comp_dev if not NULL.
+ * cur_dev, prev_dev: host arrays of nfields device pointers, each a pitched
+ * grid of the model's storage type, 16-byte aligned; prev_dev[f] is
+ * overwritten.  acc_sign: host array of nfields factors (NULL: all +1).
+ * acc_dev, comp_dev: pitched FP32 grids.  nfields in 1..32.  Asynchronous on
+ * stream. */
+wave_status wave_step(wave_model model, int32_t nfields, const void* const* cur_dev, void* const* prev_dev,
+                      const float* acc_sign, float* acc_dev, float* comp_dev, void* stream);
+
 /* ---- forward ---------------------------------------------------------------
  * Leapfrog u^{n+1} = 2u^n - u^{n-1} + dt^2/a (L u^n + f^n) for n = 1..N_s with
  * traces of levels 0..N_s written to each shot's traces_dev.

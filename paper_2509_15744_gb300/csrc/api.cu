@@ -434,6 +434,61 @@ static SparseArgs sparse_args(const wave_model_s* m, const int64_t* recp, int32_
   return a;
 }
 
+extern "C" wave_status wave_model_pitch(wave_model m, int64_t* pitch) {
+  if (!m || !pitch) return WAVE_EINVAL;
+  *pitch = m->g.px;
+  return WAVE_OK;
+}
+
+// ---------------------------------------------------------------------------
+// one step of several fields (the step of Algorithm 1's loops, no force)
+// ---------------------------------------------------------------------------
+extern "C" wave_status wave_step(wave_model m, int32_t nfields, const void* const* cur_dev, void* const* prev_dev,
+                                 const float* acc_sign, float* acc_dev, float* comp_dev, void* stream) {
+  if (!m || !cur_dev || !prev_dev || nfields < 1 || nfields > kMaxBatch) return WAVE_EINVAL;
+  if (comp_dev && !acc_dev) return WAVE_EINVAL;
+  auto misaligned = [](const void* p) { return reinterpret_cast<uintptr_t>(p) % 16 != 0; };
+  if (misaligned(acc_dev) || misaligned(comp_dev)) return WAVE_EINVAL;
+  for (int f = 0; f < nfields; ++f) {
+    if (!cur_dev[f] || !prev_dev[f] || misaligned(cur_dev[f]) || misaligned(prev_dev[f])) return WAVE_EINVAL;
+    if (cur_dev[f] == prev_dev[f]) return WAVE_EINVAL;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  const bool one_launch = m->d.ndim == 3 && m->d.physics == WAVE_VELOCITY && m->d.storage == WAVE_F32;
+  if (one_launch) {
+    BatchArgs b;
+    memset(&b, 0, sizeof(b));
+    b.base = step_args(m, nullptr, nullptr);
+    b.base.acc = acc_dev;
+    b.base.comp = comp_dev;
+    b.base.acc_scale = 1.f;
+    b.err = m->err;
+    b.wait_limit_cycles = m->wait_limit_cycles;
+    b.debug_stall = m->debug_stall;
+    b.nshots = nfields;
+    for (int f = 0; f < nfields; ++f) {
+      b.cur[f] = static_cast<const float*>(cur_dev[f]);
+      b.prev[f] = static_cast<float*>(prev_dev[f]);
+      b.accf[f] = acc_dev ? (acc_sign ? acc_sign[f] : 1.f) : 0.f;
+    }
+    CUDA_TRY(run_batched(m, b, s));
+    return WAVE_OK;
+  }
+  for (int f = 0; f < nfields; ++f) {
+    StepArgs a = step_args(m, cur_dev[f], prev_dev[f]);
+    const float sg = acc_sign ? acc_sign[f] : 1.f;
+    if (acc_dev && sg != 0.f) {
+      a.acc = acc_dev;
+      a.comp = comp_dev;
+      a.acc_scale = sg;
+      a.acc_mass = 1;
+      a.acc_stiff = 1;
+    }
+    CUDA_TRY(run_step(m, a, s));
+  }
+  return WAVE_OK;
+}
+
 // ---------------------------------------------------------------------------
 // forward
 // ---------------------------------------------------------------------------

@@ -78,6 +78,20 @@ __device__ __forceinline__ void x_terms(const float* srow, int lane, float lap[4
   }
 }
 
+// In the shared-memory ring kernels the lane's own float4 is read from the
+// staged row, whose cells at x >= nx hold mirrored ghost values; zeroing them
+// there (u = u_old = coef = 0 in the row padding) keeps the padding at zero
+// and its sensitivity increment at zero.
+__device__ __forceinline__ float4 mask_row_padding(float4 u, int64_t xl, int64_t nx) {
+  if (xl + 4 > nx) {
+    if (xl >= nx) u.x = 0.f;
+    if (xl + 1 >= nx) u.y = 0.f;
+    if (xl + 2 >= nx) u.z = 0.f;
+    if (xl + 3 >= nx) u.w = 0.f;
+  }
+  return u;
+}
+
 __device__ __forceinline__ void kahan_add(float& acc, float& comp, float v) {
   const float y = v - comp;
   const float t = acc + y;

@@ -185,7 +185,7 @@ step3d_velocity_ring_kernel(BatchArgs b) {
         }
         float lap[4];
         x_terms<R>(srow, lane, lap, 3.f * cw<R>(0));
-        const float4 u = *reinterpret_cast<const float4*>(srow + 4 + 4 * lane);
+        const float4 u = mask_row_padding(*reinterpret_cast<const float4*>(srow + 4 + 4 * lane), xl, g.nx);
   #pragma unroll
         for (int j = 1; j <= R; ++j) {
           const float4 ym = *reinterpret_cast<const float4*>(cplane + (R + warp - j) * kRowW + col);

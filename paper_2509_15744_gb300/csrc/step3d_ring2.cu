@@ -168,7 +168,7 @@ step3d_velocity_ring2_kernel(BatchArgs b) {
       }
       float lap[4];
       x_terms<R>(srow, lane, lap, 3.f * cw<R>(0));
-      const float4 u = *reinterpret_cast<const float4*>(cplane + own);
+      const float4 u = mask_row_padding(*reinterpret_cast<const float4*>(cplane + own), x0 + 4 * lane, g.nx);
       // y / z terms and the update on pairs of cells (paired FP32 ops of
       // sm_100-class GPUs; each element rounds as the scalar code would)
       float2 l01 = make_float2(lap[0], lap[1]), l23 = make_float2(lap[2], lap[3]);

@@ -248,7 +248,7 @@ step3d_velocity_tma_kernel(BatchArgs b) {
         }
         float lap[4];
         x_terms<R>(srow, lane, lap, 3.f * cw<R>(0));
-        const float4 u = *reinterpret_cast<const float4*>(srow + col);
+        const float4 u = mask_row_padding(*reinterpret_cast<const float4*>(srow + col), xl, g.nx);
         const bool zone = (z - R >= 0) && (z + R < g.nz);
 #pragma unroll
         for (int j = 1; j <= R; ++j) {

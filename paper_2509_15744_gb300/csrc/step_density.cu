@@ -137,7 +137,7 @@ step2d_density_kernel(StepArgs a) {
       Face fym = face(ui, uy_m, bi, by_m, dir && y == 0);
       Face fyp = face(ui, uy_p, bi, by_p, dir && y == g.ny - 1);
       flux[i] = (fxm.flux + fxp.flux) + (fym.flux + fyp.flux);
-      grad[i] = (fxm.grad + fxp.grad) + (fym.grad + fyp.grad);
+      grad[i] = x < g.nx ? (fxm.grad + fxp.grad) + (fym.grad + fyp.grad) : 0.f;   // row padding stays zero
     }
     float4 un;
     un.x = fmaf(ca.x, flux[0], 2.f * qu1.x - u_old.x);

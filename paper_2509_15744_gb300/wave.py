@@ -77,6 +77,8 @@ _model_get_block = _sig("wave_model_get_block", _st, _vp, C.POINTER(C.c_int64))
 _model_set_tiling = _sig("wave_model_set_tiling", _st, _vp, C.c_int64, _i32, _i32, _i32)
 _model_check = _sig("wave_model_check", _st, _vp, _vp)
 _model_set_debug = _sig("wave_model_set_debug", _st, _vp, _i32, C.c_int64)
+_model_pitch = _sig("wave_model_pitch", _st, _vp, C.POINTER(C.c_int64))
+_step = _sig("wave_step", _st, _vp, _i32, C.POINTER(_vp), C.POINTER(_vp), C.POINTER(C.c_float), _vp, _vp, _vp)
 _fwd_ws = _sig("wave_forward_workspace_size", _st, _vp, C.POINTER(ShotDesc), _i32, C.POINTER(_sz))
 _forward = _sig("wave_forward", _st, _vp, C.POINTER(ShotDesc), _i32, _vp, _vp, _vp, _sz, _vp)
 _grad_ws = _sig("wave_gradient_workspace_size", _st, _vp, C.POINTER(ShotDesc), _i32, C.POINTER(GradOpts),
@@ -274,6 +276,35 @@ class Model:
         v = C.c_int64(0)
         _check(_model_get_block(self._h, C.byref(v)), "wave_model_get_block")
         return int(v.value)
+
+    @property
+    def pitch(self) -> int:
+        """Row pitch of the resident grids (nx rounded up to 128 cells)."""
+        v = C.c_int64(0)
+        _check(_model_pitch(self._h, C.byref(v)), "wave_model_pitch")
+        return int(v.value)
+
+    def pitched_shape(self) -> tuple:
+        return tuple(self.shape[:-1]) + (self.pitch,)
+
+    def step(self, cur: Sequence[torch.Tensor], prev: Sequence[torch.Tensor], acc: Optional[torch.Tensor] = None,
+             comp: Optional[torch.Tensor] = None, acc_sign: Optional[Sequence[float]] = None, stream=None):
+        """One leapfrog step of len(cur) fields (wave_step): prev[f] <- u^{n+1};
+        acc += acc_sign[f] (u^{n+1} - u^n)^2 if acc is given.  All grids are
+        pitched ([..., pitch], see pitched_shape) and contiguous."""
+        if len(cur) != len(prev) or not 1 <= len(cur) <= 32:
+            raise ValueError("cur and prev need the same number (1..32) of fields")
+        shp = self.pitched_shape()
+        level_dtype = {"f32": torch.float32, "bf16": torch.bfloat16, "f16": torch.float16}[self.storage]
+        for t, dt in [(t, level_dtype) for t in list(cur) + list(prev)] + \
+                [(t, torch.float32) for t in (acc, comp) if t is not None]:
+            if not t.is_cuda or not t.is_contiguous() or tuple(t.shape) != shp or t.dtype != dt:
+                raise ValueError(f"grids must be contiguous CUDA {dt} tensors of shape {shp}")
+        n = len(cur)
+        ca = (_vp * n)(*[t.data_ptr() for t in cur])
+        pa = (_vp * n)(*[t.data_ptr() for t in prev])
+        sg = (C.c_float * n)(*[float(v) for v in acc_sign]) if acc_sign is not None else None
+        _check(_step(self._h, n, ca, pa, sg, _ptr(acc), _ptr(comp), _stream(stream)), "wave_step")
 
     def _ensure(self, attr, nbytes):
         ws = getattr(self, attr)

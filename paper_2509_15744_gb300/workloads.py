@@ -192,20 +192,23 @@ def workload3(n: int = 4096, nt: int = 6000, seed: int = 3, sign: float = 1.0) -
 def smooth_field_3d(rng, shape, corr_cells, lo=1500.0, hi=4500.0, nmodes=48):
     """Smooth random field from a sum of random low-wavenumber plane cosines.
 
-    Evaluated separably per mode in float32, so a 1e9-cell grid is cheap to
-    build; the correlation length is about corr_cells.
+    Each mode is separable, so the field is one float32 matrix product
+    [nz, nmodes] x [nmodes, ny*nx] and a 1e9-cell grid is cheap to build; the
+    correlation length is about corr_cells.
     """
     nz, ny, nx = shape
-    out = np.zeros(shape, np.float32)
     z = np.arange(nz, dtype=np.float32)
     y = np.arange(ny, dtype=np.float32)
     x = np.arange(nx, dtype=np.float32)
-    for _ in range(nmodes):
+    zc = np.empty((nz, nmodes), np.float32)
+    yx = np.empty((nmodes, ny * nx), np.float32)
+    for m in range(nmodes):
         kz, ky, kx = rng.normal(0.0, 1.0 / corr_cells, 3)
         ph = rng.uniform(0, 2 * np.pi, 3)
         amp = rng.normal()
-        out += (amp * np.cos(kz * z + ph[0]))[:, None, None] * \
-            (np.cos(ky * y + ph[1])[:, None] * np.cos(kx * x + ph[2])[None, :])[None, :, :]
+        zc[:, m] = amp * np.cos(kz * z + ph[0])
+        yx[m] = (np.cos(ky * y + ph[1])[:, None] * np.cos(kx * x + ph[2])[None, :]).ravel()
+    out = (zc @ yx).reshape(shape)
     lo_v, hi_v = float(out.min()), float(out.max())
     out -= lo_v
     out *= (hi - lo) / (hi_v - lo_v)
