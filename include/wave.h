@@ -184,7 +184,9 @@ wave_status wave_model_get_block(wave_model model, int64_t* zblock);
  * the shared-memory ring) and pipeline (0: per-thread cp.async copies with one
  * CTA barrier per plane; 1: TMA bulk row copies, mbarrier full/empty
  * handshakes, no CTA barrier per plane; 2: cp.async copies, two planes per
- * CTA barrier, 8 rows only).  Speed only; results are identical. */
+ * CTA barrier, 8 rows only; 3: z neighbours in a register queue, one
+ * cp.async-staged plane tile per plane, ring_depth tiles ahead).  Speed
+ * only; results are identical. */
 wave_status wave_model_set_tiling(wave_model model, int64_t zblock, int32_t tile_rows, int32_t ring_depth,
                                   int32_t pipeline);
 /* Waits for `stream` and reports whether a bounded device wait of the TMA

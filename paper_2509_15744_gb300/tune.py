@@ -1,7 +1,7 @@
 """Autotuner for the step kernel's tiling, with a JSON cache.
 
 The tiling (`wave_model_set_tiling`: z-block depth, rows per CTA, ring
-depth) changes speed only, never results.  `tune()` times a short forward
+depth, pipeline) changes speed only, never results.  `tune()` times a short forward
 pass of the given shots with each candidate (CUDA events inside libwave,
 `wave_timing_*`), keeps the fastest, applies it to the model and caches it
 under a key of (dims, shape, order, physics, storage, shots per launch).
@@ -23,7 +23,7 @@ def candidates(ndim: int, nz: int):
     if ndim == 2:
         return [(zb, 8, 3, 0) for zb in (8, 16, 32, 64, 128) if zb <= max(8, nz)]
     out = []
-    for pipe in (0, 1, 2):
+    for pipe in (0, 1, 2, 3):
         for rows in ((8,) if pipe == 2 else (8, 16)):
             for depth in (2, 3):
                 for zb in (16, 32, 64, 128):

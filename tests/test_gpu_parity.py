@@ -129,14 +129,19 @@ def test_3d_tilings_give_identical_results(W, order):
     shots = gpu_shots(W, prob, with_observed=False)
     base_tr, base_fin = m.forward(shots, return_final=True)
     g0, _, _ = m.gradient(gpu_shots(W, prob), k=2.0)
+    gr0, _, _ = m.gradient(gpu_shots(W, prob), mode="reverse")
     for zb, rows, depth, pipe in [(64, 8, 2, 0), (64, 16, 3, 0), (7, 16, 2, 0), (5, 8, 3, 0), (37, 16, 3, 0),
                                   (1, 8, 2, 0), (64, 8, 3, 1), (16, 16, 2, 1), (5, 8, 2, 1), (37, 16, 3, 1),
-                                  (1, 8, 3, 1), (64, 8, 3, 2), (7, 8, 2, 2), (1, 8, 3, 2), (37, 8, 2, 2)]:
+                                  (1, 8, 3, 1), (64, 8, 3, 2), (7, 8, 2, 2), (1, 8, 3, 2), (37, 8, 2, 2),
+                                  (64, 8, 3, 3), (7, 16, 2, 3), (1, 8, 2, 3), (37, 16, 3, 3), (9, 8, 3, 3),
+                                  (10, 8, 2, 3), (3, 16, 3, 3), (4, 8, 2, 3)]:
         m.set_tiling(zb, rows, depth, pipe)
         tr, fin = m.forward(shots, return_final=True)
         g1, _, _ = m.gradient(gpu_shots(W, prob), k=2.0)
+        gr1, _, _ = m.gradient(gpu_shots(W, prob), mode="reverse")
         assert torch.equal(tr[0], base_tr[0]) and torch.equal(fin, base_fin), (zb, rows, depth, pipe)
         assert torch.equal(g1, g0), (zb, rows, depth, pipe)
+        assert torch.equal(gr1, gr0), (zb, rows, depth, pipe)
 
 
 @pytest.mark.parametrize("bc", ["dirichlet", "neumann"])
@@ -427,7 +432,8 @@ def test_tma_pipeline_batched_matches_cp_async_ring(W, bc):
     m = gpu_model(W, prob, kahan=True)
     m.set_tiling(8, 8, 3, 0)
     g0, c0, k0 = m.gradient(gpu_shots(W, prob), batched=True, k=2.5)
-    for zb, rows, depth, pipe in [(8, 8, 3, 1), (16, 16, 2, 1), (23, 8, 2, 1), (8, 8, 3, 2), (23, 8, 2, 2)]:
+    for zb, rows, depth, pipe in [(8, 8, 3, 1), (16, 16, 2, 1), (23, 8, 2, 1), (8, 8, 3, 2), (23, 8, 2, 2),
+                                  (8, 8, 3, 3), (23, 16, 2, 3), (9, 8, 2, 3), (5, 16, 3, 3)]:
         m.set_tiling(zb, rows, depth, pipe)
         g1, c1, _ = m.gradient(gpu_shots(W, prob), batched=True, k=2.5)
         torch.cuda.synchronize()
