@@ -17,6 +17,7 @@ workload (the reference arm); it never touches the GPU.
 from __future__ import annotations
 
 import argparse
+import glob
 import hashlib
 import json
 import os
@@ -217,24 +218,23 @@ def measured_peak():
 
 
 def kernel_traffic(kernel_file, workload_name):
-    """dram bytes per launch of the step kernel from the committed ncu summary,
-    if it was taken on the current kernel source (else None)."""
-    path = os.path.join(ROOT, "profiles", "step_kernel_traffic.txt")
-    if not os.path.exists(path):
-        return None
+    """dram bytes per launch of the step kernel from a committed ncu summary
+    (profiles/*_traffic.txt) taken on the current kernel source and this
+    workload, else None."""
     src = open(os.path.join(ROOT, "paper_2509_15744_gb300", "csrc", kernel_file), "rb").read()
     digest = hashlib.sha256(src).hexdigest()[:16]
-    vals = {}
-    for line in open(path):
-        if ":" in line:
-            k, v = line.split(":", 1)
-            vals[k.strip()] = v.strip()
-    if vals.get("kernel_source_sha256_16") != digest or vals.get("workload") != workload_name:
-        return None
-    try:
-        return float(vals["dram_bytes_per_launch_full_size"])
-    except (KeyError, ValueError):
-        return None
+    for path in sorted(glob.glob(os.path.join(ROOT, "profiles", "*_traffic.txt"))):
+        vals = {}
+        for line in open(path):
+            if ":" in line and not line.startswith("#"):
+                k, v = line.split(":", 1)
+                vals[k.strip()] = v.strip()
+        if vals.get("kernel_source_sha256_16") == digest and vals.get("workload") == workload_name:
+            try:
+                return float(vals["dram_bytes_per_launch_full_size"])
+            except (KeyError, ValueError):
+                return None
+    return None
 
 
 def main():
