@@ -329,6 +329,8 @@ def main():
     plain = None
     if mode == "batched" and not args.no_plain:
         sub = shots[:2]
+        # the plain path with its own best tiling (one shot per launch)
+        plain_tiling = tune.tune(model, sub, batched=False) if not args.tiling else tiling
         model.gradient(sub, objective=wl.objective, patch_sign=wl.patch_sign)
         barrier()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -337,7 +339,9 @@ def main():
         b.record(stream)
         barrier()
         pu = float(sum(wl.ncells * n for n in wl.nt[:2]))
-        plain = {"value": pu / (a.elapsed_time(b) / 1e3) / 1e9, "unit": UNIT, "shots": 2}
+        plain = {"value": pu / (a.elapsed_time(b) / 1e3) / 1e9, "unit": UNIT, "shots": 2,
+                 "tiling": list(plain_tiling)}
+        model.set_tiling(*tiling)
 
     # ---- end to end through the public API with host buffers ------------------
     e2e = None
@@ -375,7 +379,8 @@ def main():
     if wl.physics == "density":
         kfile = "step_density.cu"
     elif wl.ndim == 3:   # the 3D FP32 step kernel of the chosen pipeline
-        kfile = {0: "step3d_ring.cu", 1: "step3d_tma.cu", 2: "step3d_ring2.cu", 3: "step3d_queue.cu"}[tiling[3]]
+        kfile = {0: "step3d_ring.cu", 1: "step3d_tma.cu", 2: "step3d_ring2.cu", 3: "step3d_queue.cu",
+                 4: "step3d_pair.cu" if mode == "batched" else "step3d_queue.cu"}[tiling[3]]
     else:
         kfile = "step_velocity.cu"
     traffic = kernel_traffic(kfile, wl.name)

@@ -185,8 +185,10 @@ wave_status wave_model_get_block(wave_model model, int64_t* zblock);
  * CTA barrier per plane; 1: TMA bulk row copies, mbarrier full/empty
  * handshakes, no CTA barrier per plane; 2: cp.async copies, two planes per
  * CTA barrier, 8 rows only; 3: z neighbours in a register queue, one
- * cp.async-staged plane tile per plane, ring_depth tiles ahead).  Speed
- * only; results are identical. */
+ * cp.async-staged plane tile per plane, ring_depth tiles ahead; 4: two shots
+ * of a batched launch per pass, lower z neighbours in registers and upper
+ * ones from the staged tiles, 16 rows only).  Speed only; results are
+ * identical. */
 wave_status wave_model_set_tiling(wave_model model, int64_t zblock, int32_t tile_rows, int32_t ring_depth,
                                   int32_t pipeline);
 /* Waits for `stream` and reports whether a bounded device wait of the TMA

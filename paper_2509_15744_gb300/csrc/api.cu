@@ -77,7 +77,8 @@ struct wave_model_s {
   int tile_rows;     // 3D ring kernel: 8 or 16 rows per CTA
   int ring_depth;    // 3D ring kernel: 2 or 3 planes copied ahead
   int pipeline;      // 3D FP32: 0 cp.async ring, 1 TMA bulk copies + mbarriers, 2 two planes per
-                     // barrier, 3 register queue in z + one shared-memory plane tile
+                     // barrier, 3 register queue in z + staged plane tiles, 4 as 3 with two
+                     // shots per pass (batched)
   int* err;          // device error word (bounded waits)
   long long wait_limit_cycles;
   int debug_stall;
@@ -255,8 +256,9 @@ wave_status wave_model_set_tiling(wave_model model, int64_t zblock, int32_t tile
   if (!model || zblock < 1) return WAVE_EINVAL;
   if (tile_rows != 8 && tile_rows != 16) return WAVE_EINVAL;
   if (ring_depth != 2 && ring_depth != 3) return WAVE_EINVAL;
-  if (pipeline < 0 || pipeline > 3) return WAVE_EINVAL;
+  if (pipeline < 0 || pipeline > 4) return WAVE_EINVAL;
   if (pipeline == 2 && tile_rows != 8) return WAVE_EINVAL;
+  if (pipeline == 4 && tile_rows != 16) return WAVE_EINVAL;
   model->zblock = zblock;
   model->tile_rows = tile_rows;
   model->ring_depth = ring_depth;

@@ -1,0 +1,355 @@
+// 3D fused leapfrog step, FP32 storage, orders 2-8, batched mode: two shots
+// advanced together in one pass of a CTA over its tile.
+//
+// Same arithmetic, element by element, as the other pipelines (Eq.
+// FDstencil1 in squared-slowness form; sensitivity increment of Algorithm 1,
+// shot A's increment added before shot B's), so results are bit-identical.
+// The mapping:
+//
+// * a CTA of 16 warps owns 16 rows x 128 cells and marches up z over a block
+//   of planes, advancing the shots of the launch two at a time; the two
+//   fields share the march: one barrier and one set of index and loop
+//   bookkeeping per plane, one load of coef and one read-modify-write of the
+//   accumulator (both increments) per cell and plane;
+// * per shot, the tile of each plane (own rows + r halo rows, 4 halo cells
+//   per side) is staged by cp.async r+1+depth planes ahead (ring depth 2 or
+//   3 of the tiling) into r+2+depth buffers: the
+//   tile of plane z gives the x and y neighbours and the own rows of planes
+//   z+1 .. z+r give the upper z neighbours; the lower ones (planes z-r ..
+//   z-1) stay in a register queue of r float4 per shot, rotated statically;
+// * staging is branch-free (precomputed chunk list, chunks outside the grid
+//   zero-filled by the copy); rows behind a Dirichlet mirror are copied
+//   negated by hand; planes above the domain are staged from their mirror
+//   images (the wall plane as zeros) and read with the mirror sign;
+// * the streaming operands of plane z+1 are loaded into registers while
+//   plane z is computed.
+// In-plane offsets are 32-bit: the launcher requires px * ny < 2^31.
+#include "stencil_common.cuh"
+
+namespace wave {
+namespace {
+
+__device__ __forceinline__ void pcp16(uint32_t sdst, const float* gsrc, uint32_t nbytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(sdst), "l"(gsrc), "r"(nbytes) : "memory");
+}
+__device__ __forceinline__ void pcp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void pcp_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+enum { kPairNone = 0, kPairSq = 1, kPairKahan = 2 };
+
+template <int R, int TY, int DX>
+struct PTile {
+  static constexpr int D = R + 1 + DX;           // planes staged ahead of the centre plane
+  static constexpr int W = D - R - 1;            // copy groups left in flight at each wait
+  static constexpr int NB = D + 1;               // tile buffers per shot
+  static constexpr int ROWS = TY + 2 * R;        // staged rows per tile
+  static constexpr int CH = kRowW / 4;           // 16-byte chunks per staged row
+  static constexpr int NT = TY * 32;             // threads
+  static constexpr int K = (ROWS * CH + NT - 1) / NT;  // chunks per thread per tile
+  static constexpr int TILE = ROWS * kRowW;      // floats per tile
+  static constexpr size_t bytes() { return (size_t)2 * NB * TILE * sizeof(float); }
+  static_assert(K <= 32, "chunk masks are 32-bit");
+};
+
+template <int R, int TY, int DX, int ACC>
+__global__ void __launch_bounds__(TY * 32, 1)
+step3d_velocity_pair_kernel(BatchArgs b) {
+  using PT = PTile<R, TY, DX>;
+  constexpr int D = PT::D;
+  constexpr int NB = PT::NB;
+  extern __shared__ __align__(16) float tiles[];   // [2][NB][TILE]
+  const StepArgs& a = b.base;
+  const Geom& g = a.g;
+  const int tid = threadIdx.x;
+  const int lane = tid & 31;
+  const int warp = tid >> 5;
+  const int z0 = (int)((int64_t)blockIdx.x * a.zblock);
+  const int z1 = (int)min((int64_t)z0 + a.zblock, g.nz);
+  const int zs_end = z1 + R;                     // planes z0 .. zs_end-1 are staged
+  const int64_t x0 = (int64_t)blockIdx.y * kStrip;
+  const int64_t ty0 = (int64_t)blockIdx.z * TY;
+  const int64_t y = ty0 + warp;
+  const int64_t xl = x0 + 4 * lane;
+  const bool row_valid = y < g.ny;
+  const bool xfix = (x0 == 0) || (x0 + kStrip + R > g.nx);
+  const int row_off = (int)(y * g.px + xl);
+  const int own = (R + warp) * kRowW + 4 + 4 * lane;   // own cells in a tile
+  const uint32_t smem0 = (uint32_t)__cvta_generic_to_shared(tiles);
+
+  // staging descriptors (as in the register-queue kernel)
+  int s_dst[PT::K];
+  int c_off[PT::K];
+  uint32_t c_sz[PT::K];
+  uint32_t cp_mask = 0, neg_mask = 0;
+#pragma unroll
+  for (int k = 0; k < PT::K; ++k) {
+    const int c = tid + k * PT::NT;
+    s_dst[k] = 0;
+    c_off[k] = 0;
+    c_sz[k] = 0;
+    if (c < PT::ROWS * PT::CH) {
+      const int rr = c / PT::CH, ch = c - rr * PT::CH;
+      const int64_t yy = ty0 - R + rr;
+      const int64_t xx = x0 - 4 + 4 * ch;
+      s_dst[k] = rr * kRowW + 4 * ch;
+      float ys = 0.f;
+      if (yy >= -R && yy < g.ny + R && xx >= 0 && xx + 4 <= g.px) {
+        const int64_t ysrc = mirror_index(yy, g.ny, g.bc, &ys);
+        c_off[k] = (int)(ysrc * g.px + xx);
+      }
+      if (ys < 0.f) {
+        neg_mask |= 1u << k;
+      } else {
+        cp_mask |= 1u << k;
+        c_sz[k] = ys > 0.f ? 16u : 0u;
+      }
+    }
+  }
+  // x ghosts of the own row: position in the staged row, mirror source, sign
+  int fx_pos = -1, fx_src = 0;
+  float fx_sgn = 0.f;
+  if (xfix) {
+    int64_t gx = 0;
+    if (lane < R && x0 == 0) {
+      gx = -1 - lane;
+      fx_pos = 3 - lane;
+    } else if (lane >= 8 && lane < 8 + R) {
+      gx = (g.nx < x0 + kStrip ? g.nx : x0 + kStrip) + (lane - 8);
+      if (gx >= g.nx) fx_pos = (int)(gx - x0 + 4);
+    }
+    if (fx_pos >= 0) {
+      const int64_t m = mirror_index(gx, g.nx, g.bc, &fx_sgn);
+      fx_src = (int)(m - x0 + 4);
+    }
+  }
+  const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
+
+  for (int s0 = 0; s0 < b.nshots; s0 += 2) {
+    const bool two = s0 + 1 < b.nshots;   // uniform: a second field in this pass
+    const float* __restrict__ ucA = b.cur[s0];
+    const float* __restrict__ ucB = two ? b.cur[s0 + 1] : b.cur[s0];
+    float* __restrict__ upA = b.prev[s0];
+    float* __restrict__ upB = two ? b.prev[s0 + 1] : b.prev[s0];
+    const float fA = b.accf[s0], fB = two ? b.accf[s0 + 1] : 0.f;
+    const bool onA = ACC != kPairNone && fA != 0.f;
+    const bool onB = ACC != kPairNone && fB != 0.f;
+    const bool acc_on = onA || onB;
+    const float scA = a.acc_scale * fA, scB = a.acc_scale * fB;
+
+    // Tiles of plane p for both fields into buffer buf; one commit group.
+    // Above the domain: the mirror source plane, positive (the wall plane
+    // of a Dirichlet box as zeros); its sign is applied when it is read.
+    auto stage = [&](int p, int buf) {
+      if (p < zs_end) {
+        float zsg = 1.f;
+        const int64_t ps = p < g.nz ? p : mirror_index(p, g.nz, g.bc, &zsg);
+        const uint32_t zmask = zsg != 0.f ? 0xffffffffu : 0u;   // 0: zero-fill every chunk
+        const int64_t pofs = ps * g.plane;
+#pragma unroll
+        for (int f = 0; f < 2; ++f) {
+          if (f == 1 && !two) break;
+          const float* src0 = (f == 0 ? ucA : ucB) + pofs;
+          const uint32_t sb = smem0 + (uint32_t)(((f * NB) + buf) * PT::TILE) * 4u;
+#pragma unroll
+          for (int k = 0; k < PT::K; ++k)
+            if (cp_mask & (1u << k)) pcp16(sb + 4u * (uint32_t)s_dst[k], src0 + c_off[k], c_sz[k] & zmask);
+          if (neg_mask) {
+            float* tb = tiles + (f * NB + buf) * PT::TILE;
+#pragma unroll
+            for (int k = 0; k < PT::K; ++k)
+              if (neg_mask & (1u << k))
+                *reinterpret_cast<float4*>(tb + s_dst[k]) =
+                    zsg != 0.f ? f4_scale(__ldg(reinterpret_cast<const float4*>(src0 + c_off[k])), -1.f) : zero4;
+          }
+        }
+      }
+      pcp_commit();
+    };
+    // sign of a staged plane above the domain (1 inside)
+    auto zsign = [&](int p) -> float {
+      if (p < g.nz) return 1.f;
+      float s;
+      mirror_index(p, g.nz, g.bc, &s);
+      return s;
+    };
+
+    // prologue: tiles of planes z0 .. z0+D-1, lower queues of plane z0
+#pragma unroll 1
+    for (int i = 0; i < D; ++i) stage(z0 + i, i);
+    float4 qa[R], qb[R];   // planes z-r .. z-1 of each field
+#pragma unroll
+    for (int i = 0; i < R; ++i) {
+      const int p = z0 - R + i;
+      float zsg;
+      const int64_t ps = mirror_index(p, g.nz, g.bc, &zsg);
+      const bool ld = row_valid && zsg != 0.f;
+      qa[i] = ld ? f4_scale(__ldg(reinterpret_cast<const float4*>(ucA + ps * g.plane + row_off)), zsg) : zero4;
+      qb[i] = (ld && two) ? f4_scale(__ldg(reinterpret_cast<const float4*>(ucB + ps * g.plane + row_off)), zsg)
+                          : zero4;
+    }
+    int64_t off = (int64_t)z0 * g.plane + row_off;
+    float4 oa = zero4, ob = zero4, cf = zero4, ac = zero4, cp = zero4;   // streams of plane z
+    auto load = [&](int64_t o, float4& uoa, float4& uob, float4& c, float4& acv, float4& cpv) {
+      uoa = *reinterpret_cast<const float4*>(upA + o);
+      if (two) uob = *reinterpret_cast<const float4*>(upB + o);
+      c = __ldg(reinterpret_cast<const float4*>(a.coef + o));
+      if (acc_on) {
+        acv = *reinterpret_cast<const float4*>(a.acc + o);
+        if (ACC == kPairKahan) cpv = *reinterpret_cast<const float4*>(a.comp + o);
+      }
+    };
+    if (row_valid) load(off, oa, ob, cf, ac, cp);
+    int bz = 0;   // buffer of plane z
+    pcp_wait<PT::W>();   // tiles of planes z0 .. z0+r have landed
+    __syncthreads();
+
+    // One field f at plane z (buffer bz; lower queue ql): new level un and
+    // the centre value u the increment is taken against.
+    auto field = [&](int f, int J, int z, int bz_, bool top, const float4 (&ql)[R], const float4& u_old,
+                     float4& u, float4& un) {
+      float* tile = tiles + (f * NB + bz_) * PT::TILE;
+      float* srow = tile + (R + warp) * kRowW;
+      u = *reinterpret_cast<const float4*>(tile + own);
+      if (xfix) {
+        const float val = (fx_pos >= 0 && fx_sgn != 0.f) ? fx_sgn * srow[fx_src] : 0.f;
+        __syncwarp();
+        if (fx_pos >= 0) srow[fx_pos] = val;
+        __syncwarp();
+        u = mask_row_padding(u, xl, g.nx);
+      }
+      float lap[4];
+      x_terms<R>(srow, lane, lap, 3.f * cw<R>(0));
+      float2 l01 = make_float2(lap[0], lap[1]), l23 = make_float2(lap[2], lap[3]);
+      int bj = bz_;
+#pragma unroll
+      for (int j = 1; j <= R; ++j) {
+        bj = bj + 1 == NB ? 0 : bj + 1;   // buffer of plane z+j
+        const float4 ym = *reinterpret_cast<const float4*>(tile + own - j * kRowW);
+        const float4 yp = *reinterpret_cast<const float4*>(tile + own + j * kRowW);
+        const float4 zm = ql[(J - j + R) % R];
+        float4 zp = *reinterpret_cast<const float4*>(tiles + (f * NB + bj) * PT::TILE + own);
+        if (top) zp = f4_scale(zp, zsign(z + j));   // mirror sign above the domain (wall tile is zero)
+        const float2 c2 = make_float2(cw<R>(j), cw<R>(j));
+        l01 = __ffma2_rn(c2, __fadd2_rn(__fadd2_rn(make_float2(ym.x, ym.y), make_float2(yp.x, yp.y)),
+                                        __fadd2_rn(make_float2(zm.x, zm.y), make_float2(zp.x, zp.y))), l01);
+        l23 = __ffma2_rn(c2, __fadd2_rn(__fadd2_rn(make_float2(ym.z, ym.w), make_float2(yp.z, yp.w)),
+                                        __fadd2_rn(make_float2(zm.z, zm.w), make_float2(zp.z, zp.w))), l23);
+      }
+      const float2 tw = make_float2(2.f, 2.f);
+      const float2 n01 = __ffma2_rn(make_float2(cf.x, cf.y), l01,
+                                    __ffma2_rn(tw, make_float2(u.x, u.y), make_float2(-u_old.x, -u_old.y)));
+      const float2 n23 = __ffma2_rn(make_float2(cf.z, cf.w), l23,
+                                    __ffma2_rn(tw, make_float2(u.z, u.w), make_float2(-u_old.z, -u_old.w)));
+      un = make_float4(n01.x, n01.y, n23.x, n23.y);
+    };
+    // acc (+ comp) += sc (un - u)^2, element order as the single-field kernels
+    auto accumulate = [&](float sc, const float4& u, const float4& un) {
+      const float d0 = un.x - u.x, d1 = un.y - u.y, d2 = un.z - u.z, d3 = un.w - u.w;
+      if (ACC == kPairKahan) {
+        kahan_add(ac.x, cp.x, sc * d0 * d0);
+        kahan_add(ac.y, cp.y, sc * d1 * d1);
+        kahan_add(ac.z, cp.z, sc * d2 * d2);
+        kahan_add(ac.w, cp.w, sc * d3 * d3);
+      } else {
+        const float2 s2 = make_float2(sc, sc);
+        const float2 e01 = make_float2(d0, d1), e23 = make_float2(d2, d3);
+        const float2 r01 = __ffma2_rn(__fmul2_rn(s2, e01), e01, make_float2(ac.x, ac.y));
+        const float2 r23 = __ffma2_rn(__fmul2_rn(s2, e23), e23, make_float2(ac.z, ac.w));
+        ac = make_float4(r01.x, r01.y, r23.x, r23.y);
+      }
+    };
+
+    for (int zb = z0; zb < z1; zb += R) {
+#pragma unroll
+      for (int J = 0; J < R; ++J) {   // lower-queue slot of plane z-j is (J-j) mod r
+        const int z = zb + J;
+        if (z < z1) {   // uniform over the CTA
+          {
+            int bn = bz + D;   // the buffer of plane z-1
+            bn -= bn >= NB ? NB : 0;
+            stage(z + D, bn);
+          }
+          float4 n_oa = oa, n_ob = ob, n_cf = cf, n_ac = ac, n_cp = cp;
+          if (row_valid && z + 1 < z1) load(off + g.plane, n_oa, n_ob, n_cf, n_ac, n_cp);
+          if (row_valid) {
+            const bool top = z + R >= g.nz;
+            float4 ua, una;
+            field(0, J, z, bz, top, qa, oa, ua, una);
+            *reinterpret_cast<float4*>(upA + off) = una;
+            float4 ubv = zero4, unb = zero4;
+            if (two) {
+              field(1, J, z, bz, top, qb, ob, ubv, unb);
+              *reinterpret_cast<float4*>(upB + off) = unb;
+            }
+            if (acc_on) {
+              if (onA) accumulate(scA, ua, una);
+              if (onB) accumulate(scB, ubv, unb);
+              *reinterpret_cast<float4*>(a.acc + off) = ac;
+              if (ACC == kPairKahan) *reinterpret_cast<float4*>(a.comp + off) = cp;
+            }
+            qa[J] = ua;   // plane z enters the lower queues in place of plane z-r
+            qb[J] = ubv;
+          }
+          oa = n_oa;
+          ob = n_ob;
+          cf = n_cf;
+          ac = n_ac;
+          cp = n_cp;
+          off += g.plane;
+          bz = bz + 1 == NB ? 0 : bz + 1;
+          pcp_wait<PT::W>();   // tiles up to plane z+1+r have landed
+          __syncthreads();
+        }
+      }
+    }
+    pcp_wait<0>();
+    __syncthreads();   // the buffers are refilled for the next pair
+  }
+}
+
+template <int R, int TY, int DX, int ACC>
+cudaError_t launch_p(const BatchArgs& b, cudaStream_t s) {
+  using PT = PTile<R, TY, DX>;
+  static bool configured = false;
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(step3d_velocity_pair_kernel<R, TY, DX, ACC>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PT::bytes());
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  const Geom& g = b.base.g;
+  dim3 grid((unsigned)((g.nz + b.base.zblock - 1) / b.base.zblock), (unsigned)((g.nx + kStrip - 1) / kStrip),
+            (unsigned)((g.ny + TY - 1) / TY));
+  step3d_velocity_pair_kernel<R, TY, DX, ACC><<<grid, TY * 32, PT::bytes(), s>>>(b);
+  count_launch();
+  return cudaGetLastError();
+}
+
+template <int R, int DX>
+cudaError_t launch_p_d(const BatchArgs& b, cudaStream_t s) {
+  bool any = false;
+  for (int i = 0; i < b.nshots; ++i) any |= b.accf[i] != 0.f;
+  if (!any) return launch_p<R, 16, DX, kPairNone>(b, s);
+  if (b.base.comp) return launch_p<R, 16, DX, kPairKahan>(b, s);
+  return launch_p<R, 16, DX, kPairSq>(b, s);
+}
+
+template <int R>
+cudaError_t launch_p_r(const BatchArgs& b, cudaStream_t s) {
+  return b.base.ring_depth == 2 ? launch_p_d<R, 1>(b, s) : launch_p_d<R, 2>(b, s);
+}
+
+}  // namespace
+
+cudaError_t launch_step3d_pair(const BatchArgs& b, int order, cudaStream_t s) {
+  switch (order) {
+    case 2: return launch_p_r<1>(b, s);
+    case 4: return launch_p_r<2>(b, s);
+    case 6: return launch_p_r<3>(b, s);
+    case 8: return launch_p_r<4>(b, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace wave

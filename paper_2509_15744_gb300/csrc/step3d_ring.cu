@@ -268,7 +268,9 @@ static cudaError_t launch_ring_r(const BatchArgs& a, cudaStream_t s) {
 
 cudaError_t launch_step3d_batched(const BatchArgs& b, int order, cudaStream_t s) {
   if (b.base.pipeline == 1) return launch_step3d_tma(b, order, s);
-  if (b.base.pipeline == 3 && b.base.g.plane < (int64_t)1 << 31) return launch_step3d_queue(b, order, s);
+  if (b.base.pipeline == 4 && b.base.g.plane < (int64_t)1 << 31 && !b.base.mix_a && !b.base.u_out)
+    return launch_step3d_pair(b, order, s);
+  if (b.base.pipeline >= 3 && b.base.g.plane < (int64_t)1 << 31) return launch_step3d_queue(b, order, s);
   if (b.base.pipeline == 2 && b.base.g.plane < (int64_t)1 << 31) return launch_step3d_ring2(b, order, s);
   switch (order) {
     case 2: return launch_ring_r<1>(b, s);

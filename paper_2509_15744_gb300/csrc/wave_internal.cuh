@@ -166,6 +166,7 @@ cudaError_t launch_step3d_batched(const BatchArgs& b, int order, cudaStream_t s)
 cudaError_t launch_step3d_tma(const BatchArgs& b, int order, cudaStream_t s);
 cudaError_t launch_step3d_ring2(const BatchArgs& b, int order, cudaStream_t s);
 cudaError_t launch_step3d_queue(const BatchArgs& b, int order, cudaStream_t s);
+cudaError_t launch_step3d_pair(const BatchArgs& b, int order, cudaStream_t s);
 
 
 // ---- sparse (source / receiver) kernel -----------------------------------

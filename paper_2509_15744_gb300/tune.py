@@ -23,8 +23,8 @@ def candidates(ndim: int, nz: int):
     if ndim == 2:
         return [(zb, 8, 3, 0) for zb in (8, 16, 32, 64, 128) if zb <= max(8, nz)]
     out = []
-    for pipe in (0, 1, 2, 3):
-        for rows in ((8,) if pipe == 2 else (8, 16)):
+    for pipe in (0, 1, 2, 3, 4):
+        for rows in ((8,) if pipe == 2 else (16,) if pipe == 4 else (8, 16)):
             for depth in (2, 3):
                 for zb in (16, 32, 64, 128):
                     if zb <= max(16, nz):

@@ -134,7 +134,8 @@ def test_3d_tilings_give_identical_results(W, order):
                                   (1, 8, 2, 0), (64, 8, 3, 1), (16, 16, 2, 1), (5, 8, 2, 1), (37, 16, 3, 1),
                                   (1, 8, 3, 1), (64, 8, 3, 2), (7, 8, 2, 2), (1, 8, 3, 2), (37, 8, 2, 2),
                                   (64, 8, 3, 3), (7, 16, 2, 3), (1, 8, 2, 3), (37, 16, 3, 3), (9, 8, 3, 3),
-                                  (10, 8, 2, 3), (3, 16, 3, 3), (4, 8, 2, 3)]:
+                                  (10, 8, 2, 3), (3, 16, 3, 3), (4, 8, 2, 3), (64, 16, 3, 4), (7, 16, 2, 4),
+                                  (1, 16, 3, 4), (37, 16, 3, 4)]:
         m.set_tiling(zb, rows, depth, pipe)
         tr, fin = m.forward(shots, return_final=True)
         g1, _, _ = m.gradient(gpu_shots(W, prob), k=2.0)
@@ -433,7 +434,8 @@ def test_tma_pipeline_batched_matches_cp_async_ring(W, bc):
     m.set_tiling(8, 8, 3, 0)
     g0, c0, k0 = m.gradient(gpu_shots(W, prob), batched=True, k=2.5)
     for zb, rows, depth, pipe in [(8, 8, 3, 1), (16, 16, 2, 1), (23, 8, 2, 1), (8, 8, 3, 2), (23, 8, 2, 2),
-                                  (8, 8, 3, 3), (23, 16, 2, 3), (9, 8, 2, 3), (5, 16, 3, 3)]:
+                                  (8, 8, 3, 3), (23, 16, 2, 3), (9, 8, 2, 3), (5, 16, 3, 3), (8, 16, 3, 4),
+                                  (23, 16, 2, 4), (5, 16, 3, 4), (1, 16, 3, 4)]:
         m.set_tiling(zb, rows, depth, pipe)
         g1, c1, _ = m.gradient(gpu_shots(W, prob), batched=True, k=2.5)
         torch.cuda.synchronize()
