@@ -1077,14 +1077,38 @@ extern "C" wave_status wave_adjoint_sensitivity(wave_model m, const wave_shot* s
       adj.resid_in = w.resid;
       adj.k_dev = kd;
       adj.weight = (float)wgt;
+      // 3D: u and lambda advance in one launch, the mixed term taken from registers
+      const bool fused = m->d.ndim == 3 && g.plane < ((int64_t)1 << 31);
       for (int j = N; j >= 1; --j) {
         fs.dst = u_n;
         fs.ilevel = j;
         CUDA_TRY(launch_sparse(fs, stor, s));
-        CUDA_TRY(run_step(m, step_args(m, u_c, u_n), s));
         adj.dst = l_n;
         adj.ilevel = j;
         CUDA_TRY(launch_sparse(adj, stor, s));
+        if (fused) {
+          BatchArgs b;
+          memset(&b, 0, sizeof(b));
+          b.base = step_args(m, nullptr, nullptr);
+          b.base.acc = w.acc;
+          b.base.acc_scale = -1.f;
+          b.err = m->err;
+          b.wait_limit_cycles = m->wait_limit_cycles;
+          b.debug_stall = m->debug_stall;
+          b.nshots = 2;
+          b.cur[0] = static_cast<const float*>(u_c);
+          b.prev[0] = static_cast<float*>(u_n);
+          b.cur[1] = static_cast<const float*>(l_c);
+          b.prev[1] = static_cast<float*>(l_n);
+          b.accf[0] = 0.f;
+          b.accf[1] = 1.f;
+          b.pair_mix = 1;
+          CUDA_TRY(run_batched(m, b, s));
+          std::swap(u_c, u_n);
+          std::swap(l_c, l_n);
+          continue;
+        }
+        CUDA_TRY(run_step(m, step_args(m, u_c, u_n), s));
         StepArgs a = step_args(m, l_c, l_n);
         a.acc = w.acc;
         a.acc_scale = -1.f;

@@ -22,7 +22,9 @@
 //   negated by hand; planes above the domain are staged from their mirror
 //   images (the wall plane as zeros) and read with the mirror sign;
 // * the streaming operands of plane z+1 are loaded into registers while
-//   plane z is computed.
+//   plane z is computed;
+// * the exact reverse-time mode runs u (field A) and lambda (field B) here
+//   and accumulates their mixed term from registers (no re-read of u).
 // In-plane offsets are 32-bit: the launcher requires px * ny < 2^31.
 #include "stencil_common.cuh"
 
@@ -36,7 +38,7 @@ __device__ __forceinline__ void pcp_commit() { asm volatile("cp.async.commit_gro
 template <int N>
 __device__ __forceinline__ void pcp_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
-enum { kPairNone = 0, kPairSq = 1, kPairKahan = 2 };
+enum { kPairNone = 0, kPairSq = 1, kPairKahan = 2, kPairMix = 3 };
 
 template <int R, int TY, int DX>
 struct PTile {
@@ -132,8 +134,8 @@ step3d_velocity_pair_kernel(BatchArgs b) {
     float* __restrict__ upA = b.prev[s0];
     float* __restrict__ upB = two ? b.prev[s0 + 1] : b.prev[s0];
     const float fA = b.accf[s0], fB = two ? b.accf[s0 + 1] : 0.f;
-    const bool onA = ACC != kPairNone && fA != 0.f;
-    const bool onB = ACC != kPairNone && fB != 0.f;
+    const bool onA = ACC != kPairNone && ACC != kPairMix && fA != 0.f;
+    const bool onB = ACC != kPairNone && (ACC == kPairMix ? two : fB != 0.f);
     const bool acc_on = onA || onB;
     const float scA = a.acc_scale * fA, scB = a.acc_scale * fB;
 
@@ -282,7 +284,15 @@ step3d_velocity_pair_kernel(BatchArgs b) {
               field(1, J, z, bz, top, qb, ob, ubv, unb);
               *reinterpret_cast<float4*>(upB + off) = unb;
             }
-            if (acc_on) {
+            if (ACC == kPairMix && acc_on) {
+              // exact reverse-time mode: field A is u, field B is lambda (Eq.
+              // kernel1 mixed term, same operand order as the one-field kernels)
+              ac.x = fmaf(scB * (ubv.x - unb.x), ua.x - una.x, ac.x);
+              ac.y = fmaf(scB * (ubv.y - unb.y), ua.y - una.y, ac.y);
+              ac.z = fmaf(scB * (ubv.z - unb.z), ua.z - una.z, ac.z);
+              ac.w = fmaf(scB * (ubv.w - unb.w), ua.w - una.w, ac.w);
+              *reinterpret_cast<float4*>(a.acc + off) = ac;
+            } else if (acc_on) {
               if (onA) accumulate(scA, ua, una);
               if (onB) accumulate(scB, ubv, unb);
               *reinterpret_cast<float4*>(a.acc + off) = ac;
@@ -328,6 +338,7 @@ cudaError_t launch_p(const BatchArgs& b, cudaStream_t s) {
 
 template <int R, int DX>
 cudaError_t launch_p_d(const BatchArgs& b, cudaStream_t s) {
+  if (b.pair_mix) return launch_p<R, 16, DX, kPairMix>(b, s);
   bool any = false;
   for (int i = 0; i < b.nshots; ++i) any |= b.accf[i] != 0.f;
   if (!any) return launch_p<R, 16, DX, kPairNone>(b, s);

@@ -25,6 +25,8 @@
 //   (negated for a Dirichlet mirror, zero on the wall node); the x ghosts of
 //   the own rows are filled warp-locally right before use;
 // * one __syncthreads per plane.
+#include <string.h>
+
 #include "stencil_common.cuh"
 
 namespace wave {
@@ -267,6 +269,9 @@ static cudaError_t launch_ring_r(const BatchArgs& a, cudaStream_t s) {
 }
 
 cudaError_t launch_step3d_batched(const BatchArgs& b, int order, cudaStream_t s) {
+  // the fused (u, lambda) pair of the exact reverse-time mode runs only in the pair kernel
+  if (b.pair_mix) return b.nshots == 2 && b.base.g.plane < (int64_t)1 << 31 ? launch_step3d_pair(b, order, s)
+                                                                           : cudaErrorInvalidValue;
   if (b.base.pipeline == 1) return launch_step3d_tma(b, order, s);
   if (b.base.pipeline == 4 && b.base.g.plane < (int64_t)1 << 31 && !b.base.mix_a && !b.base.u_out)
     return launch_step3d_pair(b, order, s);
@@ -283,6 +288,7 @@ cudaError_t launch_step3d_batched(const BatchArgs& b, int order, cudaStream_t s)
 
 cudaError_t launch_step3d_ring(const StepArgs& a, int order, cudaStream_t s) {
   BatchArgs b;
+  memset(&b, 0, sizeof(b));
   b.base = a;
   b.nshots = 1;
   b.cur[0] = reinterpret_cast<const float*>(a.u_cur);

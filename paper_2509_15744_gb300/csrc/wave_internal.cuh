@@ -157,6 +157,8 @@ struct BatchArgs {
   const float* cur[kMaxBatch];   // level n of each shot
   float* prev[kMaxBatch];        // level n-1 -> n+1 of each shot
   float accf[kMaxBatch];         // per-shot factor on acc_scale this step (0: no increment)
+  int pair_mix;                  // two fields (u, lambda) in the two-shots-per-pass kernel:
+                                 // acc += acc_scale accf[1] (lambda - lambda_new)(u - u_new)
   // TMA pipeline only:
   int* err;                      // set to 1 when a bounded wait gives up
   long long wait_limit_cycles;   // bound of every wait (clock64 cycles)
