@@ -41,6 +41,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="w2", choices=["w0", "w1", "w2", "w3", "w4"])
     ap.add_argument("--mode", default="auto", choices=["auto", "plain", "batched"])
+    ap.add_argument("--forward-curve", action="store_true",
+                    help="forward time per step versus grid size (2D and 3D, order 2) instead of the benchmark")
     ap.add_argument("--grad-mode", default="superposition", choices=["superposition", "symmetric", "reverse"],
                     help="gradient: Algorithm 1, the +-k mean, or the two-field reverse-time adjoint "
                          "(the last two are exact and run shot by shot)")
@@ -237,6 +239,42 @@ def kernel_traffic(kernel_file, workload_name):
     return None
 
 
+def forward_curve(W, torch, nt=40, warm=5):
+    """Forward solver time per step versus cells (Sec. 3.2's computation-time
+    study): 2D and 3D, order 2, velocity form, one point source and receiver,
+    device-resident inputs, CUDA events around the forward call."""
+    import numpy as np
+    dev = torch.device("cuda")
+    sides = {2: [128, 256, 512, 1024, 2048, 2896, 4096, 8192, 16384, 32768],
+             3: [32, 64, 100, 128, 160, 200, 256, 320, 400, 512, 640, 800, 1024]}
+    points = []
+    for ndim, ns in sides.items():
+        for n in ns:
+            shape = (n,) * ndim
+            cells = n ** ndim
+            dt = W.cfl_dt(ndim, 2, 10.0, 3000.0, 0.5)
+            v = torch.full(shape, 2500.0, device=dev)
+            m = W.Model(v, 10.0, dt, 2, "velocity", "dirichlet")
+            src = int(np.ravel_multi_index(tuple(s // 2 for s in shape), shape))
+            wav = W.wavelet("ricker", 15.0, dt, nt, device=dev)
+            rec = torch.tensor([src], dtype=torch.int64, device=dev)
+            warm_shot = W.Shot(src, wav[: warm + 1].contiguous(), rec)
+            m.forward([warm_shot])
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            m.forward([W.Shot(src, wav, rec)])
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / nt
+            points.append({"ndim": ndim, "cells": cells, "ms_per_step": ms, "Gcell_steps_per_s": cells / ms / 1e6,
+                           "working_set_MB": 16.0 * cells / 1e6})
+            del m, v
+            torch.cuda.empty_cache()
+    print(json.dumps({"metric": "forward time per step vs cells (order 2, velocity)", "unit": "ms",
+                      "points": points}), flush=True)
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -259,6 +297,9 @@ def main():
     import __graft_entry__ as ge
     ge.build()
     from paper_2509_15744_gb300 import wave as W
+    if args.forward_curve:
+        forward_curve(W, torch)
+        return
 
     wl = make_workload(args.workload, args.shape, args.shots, args.nt)
     dt = W.cfl_dt(wl.ndim, wl.order, wl.h, wl.vmax, wl.cfl_fraction)
