@@ -1,0 +1,81 @@
+"""Host-side logic that needs no GPU: the autotuner's candidate tilings, the
+benchmark's traffic record lookup and option parsing, and the workload
+generators' structure."""
+import hashlib
+import os
+import sys
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def test_tuner_candidates_respect_pipeline_constraints():
+    pytest.importorskip("torch")
+    from paper_2509_15744_gb300 import tune
+    c3 = tune.candidates(3, 512)
+    pipes = {c[3] for c in c3}
+    assert pipes == {0, 1, 2, 3, 4}
+    assert all(c[1] == 8 for c in c3 if c[3] == 2)      # two planes per barrier: 8 rows
+    assert all(c[1] == 16 for c in c3 if c[3] == 4)     # two shots per pass: 16 rows
+    assert all(c[2] in (2, 3) and c[0] in (16, 32, 64, 128) for c in c3)
+    c2 = tune.candidates(2, 300)
+    assert all(c[3] == 0 and c[1] == 8 for c in c2)
+    # small grids do not get z-blocks deeper than the grid
+    assert all(c[0] <= 16 for c in tune.candidates(3, 12))
+
+
+def test_traffic_record_is_used_only_for_the_current_kernel_source(tmp_path, monkeypatch):
+    sys.path.insert(0, ROOT)
+    import bench
+    csrc = tmp_path / "paper_2509_15744_gb300" / "csrc"
+    csrc.mkdir(parents=True)
+    (csrc / "k.cu").write_bytes(b"kernel v1")
+    prof = tmp_path / "profiles"
+    prof.mkdir()
+    digest = hashlib.sha256(b"kernel v1").hexdigest()[:16]
+    (prof / "k_w_traffic.txt").write_text(
+        "# comment: with a colon\n"
+        f"kernel_source_sha256_16: {digest}\nworkload: w\ndram_bytes_per_launch_full_size: 12345\n")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.kernel_traffic("k.cu", "w") == 12345.0
+    assert bench.kernel_traffic("k.cu", "other workload") is None
+    (csrc / "k.cu").write_bytes(b"kernel v2")           # the kernel changed since the capture
+    assert bench.kernel_traffic("k.cu", "w") is None
+
+
+def test_bench_options():
+    sys.path.insert(0, ROOT)
+    import bench
+    old = sys.argv
+    try:
+        sys.argv = ["bench.py", "--tiling", "64:16:2:4", "--grad-mode", "reverse", "--forward-curve"]
+        a = bench.parse()
+        assert a.tiling == "64:16:2:4" and a.grad_mode == "reverse" and a.forward_curve
+        sys.argv = ["bench.py"]
+        a = bench.parse()
+        assert a.gpus == 1 and a.warmup >= 3 and a.workload == "w2" and a.impl == "ours"
+    finally:
+        sys.argv = old
+
+
+def test_smooth_field_is_a_sum_of_separable_modes():
+    from paper_2509_15744_gb300 import workloads as WL
+    f = WL.smooth_field_3d(np.random.default_rng(4), (20, 24, 28), 50.0, lo=1500.0, hi=4500.0, nmodes=6)
+    assert f.dtype == np.float32 and f.flags["C_CONTIGUOUS"] and f.shape == (20, 24, 28)
+    assert f.min() == pytest.approx(1500.0) and f.max() == pytest.approx(4500.0, rel=1e-6)
+    # the same modes evaluated cell by cell (before the affine map to [lo, hi])
+    rng = np.random.default_rng(4)
+    z, y, x = (np.arange(n, dtype=np.float64) for n in (20, 24, 28))
+    ref = np.zeros((20, 24, 28))
+    for _ in range(6):
+        kz, ky, kx = rng.normal(0.0, 1.0 / 50.0, 3)
+        ph = rng.uniform(0, 2 * np.pi, 3)
+        amp = rng.normal()
+        ref += amp * np.cos(kz * z + ph[0])[:, None, None] * np.cos(ky * y + ph[1])[None, :, None] \
+            * np.cos(kx * x + ph[2])[None, None, :]
+    ref = 1500.0 + (ref - ref.min()) * 3000.0 / (ref.max() - ref.min())
+    np.testing.assert_allclose(f, ref, rtol=2e-5)
+    w4 = WL.workload4(n=32, nt=10)
+    assert w4.nshots == 4 and len(set(w4.sources)) == 4 and w4.receivers[0].size == 32 * 32
