@@ -137,18 +137,22 @@ def run_reference(args, rank, world):
         return
     wl = make_workload(args.workload, args.shape, args.shots, args.nt)
     crop = 192 if wl.ndim == 3 else 2048
-    rates = []
+    rates, secs = [], []
     desc = ""
     for i in range(args.warmup + args.steps):
-        r, desc, _ = oracle_sample(wl, crop=crop, nt=6)
+        r, desc, el = oracle_sample(wl, crop=crop, nt=6)
         if i >= args.warmup:
             rates.append(r)
+            secs.append(el)
     value = statistics.median(rates)
     out = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.median(secs),
+        "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": wl.name, "sample": desc},
+        "config": {"workload": wl.name, "shape": list(wl.shape), "order": wl.order, "physics": wl.physics,
+                   "shots": wl.nshots, "nt_total": int(sum(wl.nt)), "mode": "oracle sample",
+                   "sample": desc},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
