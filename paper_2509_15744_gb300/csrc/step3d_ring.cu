@@ -273,7 +273,9 @@ cudaError_t launch_step3d_batched(const BatchArgs& b, int order, cudaStream_t s)
   if (b.pair_mix) return b.nshots == 2 && b.base.g.plane < (int64_t)1 << 31 ? launch_step3d_pair(b, order, s)
                                                                            : cudaErrorInvalidValue;
   if (b.base.pipeline == 1) return launch_step3d_tma(b, order, s);
-  if (b.base.pipeline == 4 && b.base.g.plane < (int64_t)1 << 31 && !b.base.mix_a && !b.base.u_out)
+  // pipeline 4 pairs the fields of a launch; a launch of one field gains nothing from it
+  if (b.base.pipeline == 4 && b.nshots >= 2 && b.base.g.plane < (int64_t)1 << 31 && !b.base.mix_a &&
+      !b.base.u_out)
     return launch_step3d_pair(b, order, s);
   if (b.base.pipeline >= 3 && b.base.g.plane < (int64_t)1 << 31) return launch_step3d_queue(b, order, s);
   if (b.base.pipeline == 2 && b.base.g.plane < (int64_t)1 << 31) return launch_step3d_ring2(b, order, s);
