@@ -111,3 +111,22 @@ def test_workloads_are_deterministic():
     import oracle as O
     # the stated time step of workload 0 is half the 2D second-order limit
     assert abs(O.cfl_dt(a.h, a.vmax, 2, 2, a.cfl_fraction) - 0.5 * 10 / (3000 * 2 ** 0.5)) < 1e-15
+
+
+def test_plain_c_client_links_and_runs_the_host_checks(lib, tmp_path):
+    # The boundary is usable from C99 alone: tests/c_abi/host_check.c includes
+    # only wave.h, links libwave, and calls its host-side entry points.
+    import shutil
+    import subprocess
+    from paper_2509_15744_gb300 import build
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    exe = tmp_path / "host_check"
+    libdir = os.path.dirname(build.LIB)
+    subprocess.run([cc, "-std=c99", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"),
+                    os.path.join(ROOT, "tests", "c_abi", "host_check.c"), "-o", str(exe),
+                    "-L", libdir, "-l:libwave.so", f"-Wl,-rpath,{libdir}", "-lm"], check=True)
+    r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0, r.stdout + r.stderr
+    assert "ok" in r.stdout
