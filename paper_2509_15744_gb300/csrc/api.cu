@@ -97,7 +97,6 @@ static wave_status validate_desc(const wave_grid_desc* d) {
     if (d->n[a] < d->order + 1) return WAVE_EINVAL;
   if (d->ndim == 2 && d->n[2] != 1) return WAVE_EINVAL;
   if (d->physics == WAVE_DENSITY && d->order != 2) return WAVE_EINVAL;
-  if (d->physics == WAVE_DENSITY && d->ndim != 2) return WAVE_EUNSUPPORTED;
   return WAVE_OK;
 }
 

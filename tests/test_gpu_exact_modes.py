@@ -130,8 +130,9 @@ def test_symmetric_mode_lifts_the_density_patch_floor(W):
     assert sym_errs[1e-1] < 0.1 * min(sup_errs)
 
 
-def test_symmetric_density_l2(W):
-    prob = make_problem((48, 150), physics="density", bc="dirichlet", nt=200, nrec=40, seed=62)
+@pytest.mark.parametrize("shape,nt", [((48, 150), 200), ((10, 12, 131), 60)])
+def test_symmetric_density_l2(W, shape, nt):
+    prob = make_problem(shape, physics="density", bc="dirichlet", nt=nt, nrec=40, seed=62)
     m = gpu_model(W, prob, kahan=True)
     g, mis, kd = m.gradient(gpu_shots(W, prob), mode="symmetric")
     torch.cuda.synchronize()

@@ -49,6 +49,7 @@ CASES = [
     ("vel3d_o4_neumann", (12, 17, 260), "velocity", 4, "neumann", "f32"),
     ("vel2d_o6_neumann", (37, 141), "velocity", 6, "neumann", "f32"),
     ("dens2d_neumann", (30, 150), "density", 2, "neumann", "f32"),
+    ("dens3d_dirichlet", (9, 11, 131), "density", 2, "dirichlet", "f32"),
     ("vel3d_o8_bf16", (11, 13, 140), "velocity", 8, "dirichlet", "bf16"),
 ]
 

