@@ -53,6 +53,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain-path comparison")
+    ap.add_argument("--no-graph", action="store_true", help="time eager calls instead of CUDA-graph replays")
     # reduced sizes, for profiling captures only (the line is marked "reduced")
     ap.add_argument("--shape", default=None, help="override the grid shape, e.g. 256,256,256")
     ap.add_argument("--shots", type=int, default=None, help="use the first K shots")
@@ -105,21 +106,21 @@ def aggregate(ms_local, units_local, dist=None, device=None):
 
 
 # ---------------------------------------------------------------------------
-# CPU oracle sample (cpu_baseline leg and the reference arm)
+# CPU oracle sample (cpu_baseline leg and the reference arm): the FP64 oracle
+# on every host core, one process per core, each running Algorithm 1 for one
+# shot on a crop of the workload
 # ---------------------------------------------------------------------------
-def oracle_sample(wl, crop=160, nt=2):
-    """Run the oracle's Algorithm 1 (one shot, nt steps) on a crop of the
-    workload and return (gradient cell-updates/s, description)."""
+def _oracle_shot(job):
+    """One process's share: Algorithm 1 (one shot, nt steps each way) on a
+    crop; returns the seconds it took."""
     import numpy as np
     import oracle as O
-
-    shape = tuple(min(crop, s) for s in wl.shape)
-    sl = tuple(slice(0, s) for s in shape)
-    param = np.ascontiguousarray(np.asarray(wl.init_param)[sl]).astype(np.float64)
-    dt = O.cfl_dt(wl.h, wl.vmax, wl.ndim, wl.order, wl.cfl_fraction)
-    med = O.Medium(wl.physics, param, wl.h, dt, wl.order, wl.bc)
-    size = int(np.prod(shape))
-    mid = [s // 2 for s in shape]
+    physics, param, h, order, bc, vmax, cfl, nt, seed = job
+    shape = param.shape
+    dt = O.cfl_dt(h, vmax, len(shape), order, cfl)
+    med = O.Medium(physics, param, h, dt, order, bc)
+    rng = np.random.default_rng(seed)
+    mid = [int(rng.integers(n // 4, 3 * n // 4)) for n in shape]
     mid[0] = min(2, shape[0] - 1)
     src = int(np.ravel_multi_index(tuple(mid), shape))
     rec = np.arange(0, shape[-1], 2, dtype=np.int64)
@@ -127,23 +128,65 @@ def oracle_sample(wl, crop=160, nt=2):
     shot = O.Shot(src, wav, rec, np.zeros((len(rec), nt + 1)), 1.0)
     t0 = time.perf_counter()
     O.superposition_gradient(med, [shot], nt, 1.0)
-    el = time.perf_counter() - t0
-    desc = f"oracle Algorithm 1 (FP64 numpy, one shot, {nt} steps each way) on a {'x'.join(map(str, shape))} crop"
-    return size * nt / el / 1e9, desc, el
+    return time.perf_counter() - t0
+
+
+def cpu_model():
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu part")):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+class OracleSampler:
+    """The oracle's Algorithm 1 on all host cores: `procs` processes (spawned,
+    so safe after CUDA initialisation), each one shot of `nt` steps each way
+    on a crop of the workload (3D: 128^3; 2D: 1024^2)."""
+
+    def __init__(self, wl, nt=6, procs=None):
+        import multiprocessing as mp
+        import numpy as np
+        self.procs = procs or (os.cpu_count() or 1)
+        crop = 128 if wl.ndim == 3 else 1024
+        shape = tuple(min(crop, n) for n in wl.shape)
+        sl = tuple(slice(0, n) for n in shape)
+        param = np.ascontiguousarray(np.asarray(wl.init_param)[sl]).astype(np.float64)
+        self.jobs = [(wl.physics, param, wl.h, wl.order, wl.bc, wl.vmax, wl.cfl_fraction, nt, i)
+                     for i in range(self.procs)]
+        self.units = float(np.prod(shape)) * nt * self.procs
+        self.desc = (f"FP64 numpy oracle, Algorithm 1, {self.procs} processes on {self.procs} host cores "
+                     f"({cpu_model()}), each one shot of {nt} steps each way on a {'x'.join(map(str, shape))} "
+                     f"crop of the workload")
+        self.pool = mp.get_context("spawn").Pool(self.procs)
+
+    def sample(self):
+        """Wall seconds and gradient cell-updates/s of one round."""
+        t0 = time.perf_counter()
+        self.pool.map(_oracle_shot, self.jobs, chunksize=1)
+        el = time.perf_counter() - t0
+        return el, self.units / el / 1e9
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
 
 
 def run_reference(args, rank, world):
     if rank != 0:
         return
     wl = make_workload(args.workload, args.shape, args.shots, args.nt)
-    crop = 192 if wl.ndim == 3 else 2048
+    sampler = OracleSampler(wl)
     rates, secs = [], []
-    desc = ""
     for i in range(args.warmup + args.steps):
-        r, desc, el = oracle_sample(wl, crop=crop, nt=6)
+        el, r = sampler.sample()
         if i >= args.warmup:
             rates.append(r)
             secs.append(el)
+    sampler.close()
     value = statistics.median(rates)
     out = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
@@ -152,8 +195,9 @@ def run_reference(args, rank, world):
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": wl.name, "shape": list(wl.shape), "order": wl.order, "physics": wl.physics,
                    "shots": wl.nshots, "nt_total": int(sum(wl.nt)), "mode": "oracle sample",
-                   "sample": desc},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc},
+                   "sample": sampler.desc},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": sampler.procs, "kind": "oracle",
+                         "sample": sampler.desc},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(out), flush=True)
@@ -347,53 +391,79 @@ def main():
     for _ in range(args.warmup):
         model.gradient(shots, **gkw)
     barrier()
+    W.timing_enable(True)   # creates the timing events (none may be created while capturing)
+    launches_eager = W.launch_count()
+    model.gradient(shots, **gkw)
+    barrier()
+    launches_per_call = W.launch_count() - launches_eager
 
-    # ---- timed region (device-resident inputs) -------------------------------
+    # ---- the timed step: replays of the gradient call captured in a CUDA
+    # graph (the whole call: both passes, sparse kernels, misfit, k, finish);
+    # the step-kernel events are captured too, so the replays time every
+    # step launch (--no-graph: eager calls instead) --------------------------
+    stream = torch.cuda.current_stream()
+    use_graph = not args.no_graph
+    graph = None
+    W.timing_enable(True)
+    if use_graph:
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            grad, mis, kd = model.gradient(shots, **gkw)
+        graph.replay()   # one more warm-up, as a replay
+        barrier()
     clocks = ClockSampler(local)
     clocks.start()
-    launches0 = W.launch_count()
-    W.timing_enable(True)
-    stream = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if not use_graph:
+        W.timing_enable(True)
     barrier()
     torch.cuda.nvtx.range_push("timed")   # lets a profiler select the timed launches
     e0.record(stream)
     for _ in range(args.steps):
-        grad, mis, kd = model.gradient(shots, **gkw)
+        if use_graph:
+            graph.replay()
+        else:
+            grad, mis, kd = model.gradient(shots, **gkw)
     e1.record(stream)
     barrier()
     torch.cuda.nvtx.range_pop()
     ms = e0.elapsed_time(e1)
+    clk = clocks.stop()
     step_ms, step_launches, step_bytes = W.timing_read()
     W.timing_enable(False)
-    launches = W.launch_count() - launches0
-    clk = clocks.stop()
+    if use_graph:   # the events hold the last replay: one gradient call
+        kernel_ms_per_call, calls_timed = step_ms, 1
+    else:
+        kernel_ms_per_call, calls_timed = step_ms / args.steps, args.steps
+    launches = launches_per_call * args.steps
+    grad_norm = float(model.grad_norm.item())   # FP64 device reduction of the finish pass
+    misfit_val = float(mis.item())
+    k_val = float(kd.item())
+    grad = grad.clone()
+    del graph
     ms, units = aggregate(ms, units_of(wl), dist, dev)
     value = units * args.steps / (ms / 1e3) / 1e9
-    grad_norm = float(torch.linalg.vector_norm(grad.double()).item())
-    misfit_val = float(mis.item())
 
-    # ---- plain single-shot-at-a-time path on the same GPU (two shots) ---------
+    # ---- plain path (one shot per launch) over the same shots on the same GPU ------
     plain = None
     if mode == "batched" and not args.no_plain:
-        sub = shots[:2]
-        # the plain path with its own best tiling (one shot per launch)
-        plain_tiling = tune.tune(model, sub, batched=False) if not args.tiling else tiling
-        model.gradient(sub, objective=wl.objective, patch_sign=wl.patch_sign)
+        plain_tiling = tune.tune(model, shots, batched=False) if not args.tiling else tiling
         barrier()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
-        model.gradient(sub, objective=wl.objective, patch_sign=wl.patch_sign)
+        gp, mp_, kp = model.gradient(shots, objective=wl.objective, patch_sign=wl.patch_sign, k=k_val)
         b.record(stream)
         barrier()
-        pu = float(sum(wl.ncells * n for n in wl.nt[:2]))
-        plain = {"value": pu / (a.elapsed_time(b) / 1e3) / 1e9, "unit": UNIT, "shots": 2,
-                 "tiling": list(plain_tiling)}
+        plain = {"value": units_of(wl) / (a.elapsed_time(b) / 1e3) / 1e9, "unit": UNIT, "shots": wl.nshots,
+                 "tiling": list(plain_tiling),
+                 "grad_rel_diff_vs_batched": float(torch.linalg.vector_norm((gp - grad).double()).item()) /
+                 max(grad_norm, 1e-300)}
         model.set_tiling(*tiling)
 
     # ---- end to end through the public API with host buffers ------------------
     e2e = None
     if not args.no_e2e:
+        e2e_steps = min(args.steps, 3)
         h_param = torch.from_numpy(np.ascontiguousarray(wl.init_param, dtype=np.float32)).pin_memory()
         h_obs = [o.cpu().pin_memory() if o is not None else None for o in observed]
         h_wav = [w.cpu().pin_memory() for w in wavs]
@@ -405,7 +475,7 @@ def main():
         d2h = h_grad.numel() * 4 + 8
         barrier()
         t0 = time.perf_counter()
-        for _ in range(args.steps):
+        for _ in range(e2e_steps):
             p = h_param.to(dev, non_blocking=True)
             sh = [W.Shot(wl.sources[i], h_wav[i].to(dev, non_blocking=True), h_rec[i].to(dev, non_blocking=True),
                          h_obs[i].to(dev, non_blocking=True) if h_obs[i] is not None else None)
@@ -418,8 +488,9 @@ def main():
             torch.cuda.synchronize()
         barrier()
         el, _ = aggregate(time.perf_counter() - t0, 0.0, dist, dev)
-        e2e = {"value": units * args.steps / el / 1e9, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
-               "d2h_bytes_per_step": int(d2h)}
+        e2e = {"value": units * e2e_steps / el / 1e9, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h), "steps": e2e_steps,
+               "mode": "eager calls: model built from host buffers every step"}
 
     # ---- roofline of the dominant kernel (the fused step) ---------------------
     peak, peak_kind = measured_peak()
@@ -427,23 +498,35 @@ def main():
     if wl.physics == "density":
         kfile = "step_density.cu"
     elif wl.ndim == 3:   # the 3D FP32 step kernel of the chosen pipeline
-        kfile = {0: "step3d_ring.cu", 1: "step3d_tma.cu", 2: "step3d_ring2.cu", 3: "step3d_queue.cu",
-                 4: "step3d_pair.cu" if mode == "batched" else "step3d_queue.cu"}[tiling[3]]
+        kfile = {0: "step3d_ring.cu", 3: "step3d_queue.cu",
+                 4: "step3d_pair.cu" if mode == "batched" else "step3d_queue.cu",
+                 5: "step3d_stream.cu" if mode == "batched" else "step3d_queue.cu"}[tiling[3]]
     else:
         kfile = "step_velocity.cu"
     traffic = kernel_traffic(kfile, wl.name)
+    nl = max(step_launches, 1)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "peak_source": peak_kind,
                 "traffic": traffic,
-                "algorithmic_bytes_per_launch": step_bytes / max(step_launches, 1),
-                "kernel": kfile.replace(".cu", ""), "launches": step_launches,
-                "avg_launch_ms": step_ms / max(step_launches, 1),
-                "kernel_share_of_step": step_ms / ms if ms > 0 else None}
+                "algorithmic_bytes_per_launch": step_bytes / nl,
+                "kernel": kfile.replace(".cu", ""), "launches_per_call": step_launches,
+                "avg_launch_ms": step_ms / nl,
+                "kernel_share_of_step": kernel_ms_per_call / (ms / args.steps) if ms > 0 else None,
+                "timing": "CUDA events around every step launch of the last timed call"
+                          if use_graph else "CUDA events around every step launch of the timed calls"}
+    if traffic:
+        # DRAM bytes actually moved, over the same launch time (re-reads count here)
+        roofline["dram_achieved"] = traffic / (step_ms / nl / 1e3) / 1e9
+        roofline["dram_frac"] = roofline["dram_achieved"] / peak
+        roofline["traffic_source"] = "ncu capture on a smaller case of the same kernel, scaled by shot-cells"
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        r, desc, _ = oracle_sample(wl, crop=192 if wl.ndim == 3 else 2048, nt=6)
-        cpu = {"value": r, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc}
+        sampler = OracleSampler(wl)
+        sampler.sample()                 # worker start-up and imports
+        _, r = sampler.sample()
+        sampler.close()
+        cpu = {"value": r, "unit": UNIT, "cores": sampler.procs, "kind": "oracle", "sample": sampler.desc}
 
     if rank == 0:
         out = {
@@ -451,12 +534,13 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": wl.name, "shape": list(wl.shape), "order": wl.order, "physics": wl.physics,
-                       "shots": wl.nshots, "nt_total": int(sum(wl.nt)), "mode": mode,
+                       "shots": wl.nshots, "nt_total": int(sum(wl.nt)),
+                       "mode": mode + (", graph replay" if use_graph else ", eager calls"),
                        "gradient": args.grad_mode, "kahan": args.kahan,
                        "storage": "f32", "parallelism": f"replicas x{world}", "tiling": list(tiling),
                        "l2": "inputs larger than L2 (each resident grid > 129 MB)"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "gpu_launches": int(launches),
-            "plain": plain, "check": {"misfit": misfit_val, "grad_l2": grad_norm, "k": float(kd.item())},
+            "plain": plain, "check": {"misfit": misfit_val, "grad_l2": grad_norm, "k": k_val},
         }
         print(json.dumps(out), flush=True)
     if dist is not None:

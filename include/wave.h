@@ -125,9 +125,27 @@ typedef struct {
   int32_t grad_wrt;    /* wave_grad_wrt */
   double patch_sign;   /* +1 suppress / -1 amplify (Sec. 5.2 sign flip); patch objective only */
   double k;            /* superposition factor (Eq. superposedforce); <= 0 selects it automatically */
-  double k_ratio;      /* automatic k = k_ratio * ||psi|| / ||f_adj|| of the first shot;
-                          0 -> 1e-2 (WAVE_SUPERPOSITION) or 1 (WAVE_SYMMETRIC_K, which has no k^2 gap) */
+  double k_ratio;      /* automatic k = k_ratio * ||psi|| / ||f_adj|| of the first shot, a stand-in
+                          for the calibration of Sec. 4.1 (the smallest k at which FP32 still agrees
+                          with FP64); 0 -> the default: 1e-2 for WAVE_SUPERPOSITION in the velocity
+                          form, 5e-2 in the density form (larger FP32 cancellation), 1 for
+                          WAVE_SYMMETRIC_K (no k^2 gap) */
 } wave_gradient_opts;
+
+/* Per-call figures of a gradient call (wave_gradient_metrics_read). */
+typedef struct {
+  double misfit;        /* C summed over shots (Eq. cost1 / cost2), FP64 */
+  double k;             /* k used (0 for WAVE_EXACT_STORED and WAVE_EXACT_REVERSE) */
+  double grad_l2;       /* ||grad||_2 of the returned gradient, FP64 reduction on the device */
+  double forward_ms;    /* device time of the forward pass(es), misfit and k included */
+  double adjoint_ms;    /* device time of the superposed / adjoint pass(es) and the finish */
+  double total_ms;      /* device time of the whole call */
+  double step_bytes;    /* algorithmic bytes of the step-kernel launches (per cell and launch:
+                           read u^n, u^{n-1}, coef [, b], write u^{n+1} per field, accumulator
+                           [+ compensation] read-modify-write once) */
+  double cell_updates;  /* sum over shots of cells x N_s: the gradient cell-updates of the call */
+  int64_t step_launches;
+} wave_gradient_metrics;
 
 typedef struct wave_model_s* wave_model;
 
@@ -144,7 +162,11 @@ uint64_t wave_launch_count(void);
  * returns the summed kernel time, the number of timed launches and their
  * algorithmic bytes (per cell: read u^n, u^{n-1}, coef [+ b], write u^{n+1},
  * [+ accumulator RMW, + compensation RMW]).  Enabling resets the counters.
- * Not thread-safe; not for use under stream capture. */
+ * The events are recorded as external events (cudaEventRecordExternal): a
+ * call captured into a CUDA graph while timing is enabled records them at
+ * each replay, and wave_timing_read then returns the last replay's kernel
+ * times with the launch and byte counts of the one captured call.
+ * Not thread-safe. */
 wave_status wave_timing_enable(int32_t on);
 wave_status wave_timing_read(double* step_ms, uint64_t* step_launches, double* step_bytes);
 
@@ -168,7 +190,8 @@ wave_status wave_wavelet(int32_t kind, double freq, int32_t nc, double psi0, dou
  * param_dev: dense [nz][ny][nx] FP32 (v in m/s, or gamma).  It must stay valid
  * while the model is used (the dC/dv chain rule reads it).  Create checks the
  * stability bound on the device and waits for that one number
- * (WAVE_EUNSTABLE if violated).  Destroy frees only the host handle. */
+ * (WAVE_EUNSTABLE if violated, WAVE_ENONFINITE if param holds a NaN or an
+ * Inf).  Destroy frees only the host handle. */
 wave_status wave_model_workspace_size(const wave_grid_desc* desc, size_t* bytes);
 wave_status wave_model_create(const wave_grid_desc* desc, const float* param_dev,
                               void* workspace_dev, size_t ws_bytes, void* stream,
@@ -180,22 +203,31 @@ wave_status wave_model_destroy(wave_model model);
 wave_status wave_model_set_block(wave_model model, int64_t zblock);
 wave_status wave_model_get_block(wave_model model, int64_t* zblock);
 /* Full tiling of the 3D FP32 step kernel: zblock as above, tile_rows (8 or 16
- * rows of 128 cells per CTA), ring_depth (2 or 3 planes staged ahead in
- * the shared-memory ring) and pipeline (0: per-thread cp.async copies with one
- * CTA barrier per plane; 1: TMA bulk row copies, mbarrier full/empty
- * handshakes, no CTA barrier per plane; 2: cp.async copies, two planes per
- * CTA barrier, 8 rows only; 3: z neighbours in a register queue, one
- * cp.async-staged plane tile per plane, ring_depth tiles ahead; 4: two shots
- * of a batched launch per pass, lower z neighbours in registers and upper
- * ones from the staged tiles, 16 rows only).  Speed only; results are
- * identical. */
+ * rows of 128 cells per CTA), ring_depth (2 or 3 planes staged ahead) and
+ * pipeline: 0: per-thread cp.async copies into a shared-memory plane ring
+ * with one CTA barrier per plane (64-bit offsets: any grid size); 3: z
+ * neighbours in a register queue, one cp.async-staged plane tile per plane;
+ * 4: two fields of a batched launch per pass, lower z neighbours in
+ * registers and upper ones from the staged tiles, 16 rows only; 5: as 4 with
+ * the tiles copied by TMA tensor copies into an mbarrier ring over z-blocks
+ * of 8 planes (zblock ignored), 16 rows only -- the default.  Pipelines 3-5
+ * send a launch of one field to the register-queue kernel.  Speed only;
+ * results are identical. */
 wave_status wave_model_set_tiling(wave_model model, int64_t zblock, int32_t tile_rows, int32_t ring_depth,
                                   int32_t pipeline);
-/* Waits for `stream` and reports whether a bounded device wait of the TMA
- * pipeline gave up since the last check (WAVE_ETIMEOUT; the results of that
- * call are invalid).  Clears the error word. */
+/* Waits for `stream` and reports whether a bounded device wait of a step
+ * kernel gave up since the last check (WAVE_ETIMEOUT; the results of that
+ * call are invalid; the error word is cleared), else whether the parameter of
+ * the last wave_model_set_param (or create) breaks the stability bound
+ * (WAVE_EUNSTABLE) or holds a NaN or Inf (WAVE_ENONFINITE). */
 wave_status wave_model_check(wave_model model, void* stream);
-/* Test hook: stall_pipeline = 1 makes the TMA pipeline issue no copies, so
+/* New parameter values for an existing model (e.g. one optimisation step):
+ * recomputes the coefficients and the stability maximum on `stream` without
+ * waiting (wave_model_check reports the outcome).  param_dev: dense FP32 grid
+ * of the model's shape; it replaces the create-time param (also for the dC/dv
+ * chain rule) and must stay valid while the model is used. */
+wave_status wave_model_set_param(wave_model model, const float* param_dev, void* stream);
+/* Test hook: stall_pipeline = 1 makes the TMA-tiled pipeline issue no copies, so
  * its first wait runs out after wait_limit_cycles (default about 4e9 cycles);
  * used to test the time-out path without a hang.  Not for production use. */
 wave_status wave_model_set_debug(wave_model model, int32_t stall_pipeline, int64_t wait_limit_cycles);
@@ -241,7 +273,9 @@ wave_status wave_forward(wave_model model, const wave_shot* shots, int32_t nshot
  * accumulating +K(u^s,u^s); K~ = difference / 2k (Eq. superposedkernel).
  * grad_dev: dense FP32 grid, summed over shots, w.r.t. opts->grad_wrt.
  * misfit_dev: one double, C summed over shots.  k_dev: one double, the k used
- * (all shots share it).  Exact mode (velocity form, FP32 storage, one shot at
+ * (all shots share it).  grad_norm_dev: NULL or one double receiving
+ * ||grad_dev||_2, reduced in FP64 on the device by the finish pass
+ * (deterministic: fixed partial sums in a fixed order).  Exact mode (velocity form, FP32 storage, one shot at
  * a time) stores the forward history u^0..u^{N+1} instead and returns the
  * standard adjoint gradient; k_dev then receives 0.
  * WAVE_SYMMETRIC_K: the forward accumulates nothing; two superposed fields
@@ -257,8 +291,23 @@ wave_status wave_gradient_workspace_size(wave_model model, const wave_shot* shot
                                          const wave_gradient_opts* opts, size_t* bytes);
 wave_status wave_adjoint_sensitivity(wave_model model, const wave_shot* shots, int32_t nshots,
                                      const wave_gradient_opts* opts, float* grad_dev,
-                                     double* misfit_dev, double* k_dev,
+                                     double* misfit_dev, double* k_dev, double* grad_norm_dev,
                                      void* workspace_dev, size_t ws_bytes, void* stream);
+
+/* ---- per-call metrics --------------------------------------------------------
+ * wave_model_set_metrics(model, 1) makes every later gradient call on the model
+ * record CUDA events at its pass boundaries (forward, superposed / adjoint,
+ * finish) on its stream; 0 (the default) records nothing.  Not for use while
+ * the stream is being captured into a CUDA graph.
+ * wave_gradient_metrics_read waits for the last gradient call on the model and
+ * fills *out: C, k, ||grad||_2 (the FP64 device reduction of the finish pass),
+ * device times per pass, the algorithmic bytes of the step launches and the
+ * cell-updates.  The call's workspace must not have been reused since.
+ * Returns WAVE_EINVAL when metrics are off or no call was recorded, and
+ * WAVE_ENONFINITE (after filling *out) when C, k or ||grad|| is not finite:
+ * the optional end-of-call check for NaN or Inf results. */
+wave_status wave_model_set_metrics(wave_model model, int32_t on);
+wave_status wave_gradient_metrics_read(wave_model model, wave_gradient_metrics* out);
 
 /* ---- misfit ----------------------------------------------------------------
  * out_dev[0] = 0.5 * weight * dt * sum_i (syn_i - obs_i)^2 in FP64 over count
@@ -281,8 +330,11 @@ wave_status misfit(const float* syn_dev, const float* obs_dev, int64_t count, do
  * before any work is enqueued.  Allocates nothing.  All calls on a GPU share
  * the array: calls whose kernels may overlap on the GPU (e.g. on unordered
  * streams) race and must not be issued.  The first call on a device looks up
- * the array's address (cudaGetSymbolAddress, with that device current); make
- * it before any stream capture starts. */
+ * the array's address (cudaGetSymbolAddress, with that device current) and
+ * caches it with the device's context (a call in a new context after a
+ * device reset looks it up again); make the first call before any stream
+ * capture starts.  WAVE_ECUDA leaves the failing call's text in
+ * wave_last_error(). */
 wave_status wave_misfit_static(const float* syn_dev, const float* obs_dev, int64_t count, double dt,
                                double weight, double* out_dev, void* stream);
 

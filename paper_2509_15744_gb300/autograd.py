@@ -37,6 +37,10 @@ class WaveProblem:
     batched: bool = False
     mode: str = "superposition"
     last_k: Optional[float] = field(default=None, init=False)
+    # the model is built (with its one host wait, the stability check) on the
+    # first call and receives later parameters without a wait; model.check()
+    # reports an unstable or non-finite parameter
+    model: Optional[W.Model] = field(default=None, init=False, repr=False)
 
 
 class WaveGradient(torch.autograd.Function):
@@ -48,8 +52,17 @@ class WaveGradient(torch.autograd.Function):
 
     @staticmethod
     def forward(ctx, param: torch.Tensor, problem: WaveProblem):
-        model = W.Model(param.detach().contiguous(), problem.h, problem.dt, problem.order, problem.physics,
-                        problem.bc, storage=problem.storage, kahan=problem.kahan)
+        p = param.detach().contiguous()
+        model = problem.model
+        key = (tuple(p.shape), p.device, problem.h, problem.dt, problem.order, problem.physics, problem.bc,
+               problem.storage, problem.kahan)
+        if model is None or getattr(model, "_problem_key", None) != key:
+            model = W.Model(p, problem.h, problem.dt, problem.order, problem.physics, problem.bc,
+                            storage=problem.storage, kahan=problem.kahan)
+            model._problem_key = key
+            problem.model = model
+        else:
+            model.set_param(p)
         grad, mis, kd = model.gradient(problem.shots, objective=problem.objective, k=problem.k,
                                        k_ratio=problem.k_ratio, mode=problem.mode, batched=problem.batched,
                                        grad_wrt="param", patch_sign=problem.patch_sign)
@@ -60,8 +73,6 @@ class WaveGradient(torch.autograd.Function):
     @staticmethod
     def backward(ctx, grad_out: torch.Tensor):
         (grad,) = ctx.saved_tensors
-        if grad_out.numel() == 1 and bool((grad_out == 1).item()):
-            return grad, None
         return grad * grad_out.to(grad.dtype), None
 
 

@@ -20,6 +20,10 @@ uint64_t launches();
 
 static thread_local std::string g_last_error;
 
+void wave::set_last_error(const char* what, cudaError_t e) {
+  g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
+}
+
 #define CUDA_TRY(expr)                                            \
   do {                                                            \
     cudaError_t _e = (expr);                                      \
@@ -76,14 +80,48 @@ struct wave_model_s {
   int64_t zblock;
   int tile_rows;     // 3D ring kernel: 8 or 16 rows per CTA
   int ring_depth;    // 3D ring kernel: 2 or 3 planes copied ahead
-  int pipeline;      // 3D FP32: 0 cp.async ring, 1 TMA bulk copies + mbarriers, 2 two planes per
-                     // barrier, 3 register queue in z + staged plane tiles, 4 as 3 with two
-                     // shots per pass (batched)
+  int pipeline;      // 3D FP32: 0 cp.async ring (any size), 3 register queue in z + staged plane tiles,
+                     // 4 as 3 with two shots per pass (batched), 5 as 4 with TMA tensor tiles
   int* err;          // device error word (bounded waits)
+  float* part;       // stability partial maxima
+  float* maxv;       // stability: max over cells of (v dt / h)^2 S-scaled (<= 4 is stable)
+  double sym;        // the operator's symbol scale used by the stability kernel
   long long wait_limit_cycles;
   int debug_stall;
   double stability;
+  // per-call metrics (wave_model_set_metrics): CUDA events at the pass
+  // boundaries of the last gradient call and where its device scalars live
+  struct Metrics {
+    bool on = false;
+    bool valid = false;
+    std::vector<cudaEvent_t> ev;
+    std::vector<int> kind;      // kEv* of each recorded event
+    size_t used = 0;
+    double bytes = 0.0;         // algorithmic bytes of the step launches
+    double units = 0.0;         // sum_s ncells * N_s
+    uint64_t launches = 0;
+    const double* scal = nullptr;   // [0] k, [4] sum grad^2, [6] C
+    int mode = 0;
+  };
+  mutable Metrics met;
 };
+
+enum { kEvStart = 0, kEvForwardEnd = 1, kEvAdjointEnd = 2 };
+
+// Record a pass boundary of the current gradient call (metrics on only).
+static cudaError_t mark(const wave_model_s* m, int kind, cudaStream_t s) {
+  auto& M = m->met;
+  if (!M.on) return cudaSuccess;
+  if (M.used == M.ev.size()) {
+    cudaEvent_t e;
+    cudaError_t err = cudaEventCreate(&e);
+    if (err != cudaSuccess) return err;
+    M.ev.push_back(e);
+  }
+  if (M.kind.size() <= M.used) M.kind.resize(M.used + 1);
+  M.kind[M.used] = kind;
+  return cudaEventRecord(M.ev[M.used++], s);
+}
 
 static wave_status validate_desc(const wave_grid_desc* d) {
   if (!d) return WAVE_EINVAL;
@@ -213,6 +251,7 @@ wave_status wave_model_create(const wave_grid_desc* desc, const float* param_dev
   float host_max = 0.f;
   CUDA_TRY(cudaMemcpyAsync(&host_max, maxv, sizeof(float), cudaMemcpyDeviceToHost, s));
   CUDA_TRY(cudaStreamSynchronize(s));
+  if (!isfinite(host_max)) return WAVE_ENONFINITE;   // a NaN or Inf parameter
   if (!(host_max <= 4.0f * (1.0f + 1e-5f))) return WAVE_EUNSTABLE;
   wave_model_s* m = new wave_model_s;
   m->d = *desc;
@@ -221,10 +260,15 @@ wave_status wave_model_create(const wave_grid_desc* desc, const float* param_dev
   m->coef = coef;
   m->bmat = bmat;
   m->zblock = default_zblock(g);
-  m->tile_rows = 8;
-  m->ring_depth = 3;
-  m->pipeline = 0;
+  // untuned default: one field per launch on the register-queue kernel, two
+  // or more on the TMA-tiled two-fields-per-pass kernel
+  m->tile_rows = 16;
+  m->ring_depth = 2;
+  m->pipeline = 5;
   m->err = errw;
+  m->part = part;
+  m->maxv = maxv;
+  m->sym = sym;
   m->wait_limit_cycles = 4000000000LL;  // about two seconds at the maximum SM clock
   m->debug_stall = 0;
   m->stability = host_max;
@@ -233,6 +277,8 @@ wave_status wave_model_create(const wave_grid_desc* desc, const float* param_dev
 }
 
 wave_status wave_model_destroy(wave_model model) {
+  if (model)
+    for (cudaEvent_t e : model->met.ev) cudaEventDestroy(e);
   delete model;
   return WAVE_OK;
 }
@@ -255,9 +301,8 @@ wave_status wave_model_set_tiling(wave_model model, int64_t zblock, int32_t tile
   if (!model || zblock < 1) return WAVE_EINVAL;
   if (tile_rows != 8 && tile_rows != 16) return WAVE_EINVAL;
   if (ring_depth != 2 && ring_depth != 3) return WAVE_EINVAL;
-  if (pipeline < 0 || pipeline > 4) return WAVE_EINVAL;
-  if (pipeline == 2 && tile_rows != 8) return WAVE_EINVAL;
-  if (pipeline == 4 && tile_rows != 16) return WAVE_EINVAL;
+  if (pipeline != 0 && (pipeline < 3 || pipeline > 5)) return WAVE_EINVAL;
+  if ((pipeline == 4 || pipeline == 5) && tile_rows != 16) return WAVE_EINVAL;
   model->zblock = zblock;
   model->tile_rows = tile_rows;
   model->ring_depth = ring_depth;
@@ -269,13 +314,35 @@ wave_status wave_model_check(wave_model model, void* stream) {
   if (!model) return WAVE_EINVAL;
   cudaStream_t s = (cudaStream_t)stream;
   int host = 0;
+  float mx = 0.f;
   CUDA_TRY(cudaMemcpyAsync(&host, model->err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaMemcpyAsync(&mx, model->maxv, sizeof(float), cudaMemcpyDeviceToHost, s));
   CUDA_TRY(cudaStreamSynchronize(s));
   if (host) {
     CUDA_TRY(cudaMemsetAsync(model->err, 0, sizeof(int), s));
     CUDA_TRY(cudaStreamSynchronize(s));
     return WAVE_ETIMEOUT;
   }
+  if (!isfinite(mx)) return WAVE_ENONFINITE;
+  if (!(mx <= 4.0f * (1.0f + 1e-5f))) return WAVE_EUNSTABLE;
+  return WAVE_OK;
+}
+
+// New parameter values for an existing model (an optimisation step): the
+// coefficients and the stability maximum are recomputed on the stream with no
+// host wait; wave_model_check reports an unstable or non-finite parameter.
+wave_status wave_model_set_param(wave_model m, const float* param_dev, void* stream) {
+  if (!m || !param_dev) return WAVE_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  const wave_grid_desc* desc = &m->d;
+  if (desc->physics == WAVE_VELOCITY)
+    CUDA_TRY(launch_coef_velocity(m->g, param_dev, (float)(desc->dt / desc->h), m->coef, s));
+  else
+    CUDA_TRY(launch_coef_density(m->g, param_dev, desc->dt * desc->dt / (desc->h * desc->h), m->coef, m->bmat, s));
+  const int nparts = 1024;
+  CUDA_TRY(launch_stability(m->g, desc->physics, m->sym, m->coef, m->bmat, m->part, nparts, s));
+  CUDA_TRY(launch_max_final(m->part, nparts, m->maxv, s));
+  m->param = param_dev;
   return WAVE_OK;
 }
 
@@ -328,7 +395,9 @@ static StepArgs step_args(const wave_model_s* m, const void* cur, void* prev) {
 }
 
 // ---- optional per-launch timing of the step kernel (CUDA events on the
-// launching stream), read back by wave_timing_read ----------------------------
+// launching stream), read back by wave_timing_read.  The events are recorded
+// as external events, so a gradient call captured into a CUDA graph records
+// them at every replay (the last replay's times are read) -------------------
 struct StepTiming {
   bool on = false;
   std::vector<cudaEvent_t> ev;
@@ -359,14 +428,18 @@ static cudaError_t run_step(const wave_model_s* m, const StepArgs& a, cudaStream
     e0 = g_timing.ev[g_timing.used];
     e1 = g_timing.ev[g_timing.used + 1];
     g_timing.used += 2;
-    cudaEventRecord(e0, s);
+    cudaEventRecordWithFlags(e0, s, cudaEventRecordExternal);
   }
   cudaError_t err = m->d.physics == WAVE_VELOCITY ? launch_step_velocity(a, m->d.order, m->d.storage, s)
                                                   : launch_step_density(a, m->d.storage, s);
   if (g_timing.on) {
-    cudaEventRecord(e1, s);
+    cudaEventRecordWithFlags(e1, s, cudaEventRecordExternal);
     g_timing.bytes += step_bytes(m, a);
     g_timing.launches += 1;
+  }
+  if (m->met.on) {
+    m->met.bytes += step_bytes(m, a);
+    m->met.launches += 1;
   }
   return err;
 }
@@ -383,18 +456,22 @@ static cudaError_t run_batched(const wave_model_s* m, const BatchArgs& b, cudaSt
     e0 = g_timing.ev[g_timing.used];
     e1 = g_timing.ev[g_timing.used + 1];
     g_timing.used += 2;
-    cudaEventRecord(e0, s);
+    cudaEventRecordWithFlags(e0, s, cudaEventRecordExternal);
   }
   cudaError_t err = launch_step3d_batched(b, m->d.order, s);
+  const double cells = (double)(m->g.nx * m->g.ny * m->g.nz);
+  bool any = false;
+  for (int i = 0; i < b.nshots; ++i) any |= b.accf[i] != 0;
+  // per shot: read u^n, u^{n-1}, write u^{n+1}; once: coef, acc (+comp) RMW
+  const double bytes = cells * (12.0 * b.nshots + 4.0 + (any ? (b.base.comp ? 16.0 : 8.0) : 0.0));
   if (g_timing.on) {
-    cudaEventRecord(e1, s);
-    const double cells = (double)(m->g.nx * m->g.ny * m->g.nz);
-    bool any = false;
-    for (int i = 0; i < b.nshots; ++i) any |= b.accf[i] != 0;
-    // per shot: read u^n, u^{n-1}, write u^{n+1}; once: coef, acc (+comp) RMW
-    double per_cell = 12.0 * b.nshots + 4.0 + (any ? (b.base.comp ? 16.0 : 8.0) : 0.0);
-    g_timing.bytes += cells * per_cell;
+    cudaEventRecordWithFlags(e1, s, cudaEventRecordExternal);
+    g_timing.bytes += bytes;
     g_timing.launches += 1;
+  }
+  if (m->met.on) {
+    m->met.bytes += bytes;
+    m->met.launches += 1;
   }
   return err;
 }
@@ -593,7 +670,7 @@ struct GradWs {
   float* resid;
   int64_t* recp;
   double* parts;
-  double* scal;  // [0] k, [1] psi2, [2] e2
+  double* scal;  // [0] k, [1] psi2, [2] e2, [3] C (no caller buffer), [4] sum grad^2, [6] C copy
 };
 
 static void carve_gradient(Carve& c, const wave_model_s* m, const wave_shot* shots, int32_t nshots, int mode,
@@ -615,7 +692,7 @@ static void carve_gradient(Carve& c, const wave_model_s* m, const wave_shot* sho
   w->resid = c.take<float>(maxres);
   w->recp = c.take<int64_t>(maxrec);
   w->parts = c.take<double>(1024);
-  w->scal = c.take<double>(4);
+  w->scal = c.take<double>(8);
 }
 
 static wave_status validate_opts(const wave_model_s* m, const wave_gradient_opts* o) {
@@ -630,6 +707,17 @@ static wave_status validate_opts(const wave_model_s* m, const wave_gradient_opts
   if (o->batched && !(m->d.ndim == 3 && m->d.physics == WAVE_VELOCITY && m->d.storage == WAVE_F32))
     return WAVE_EUNSUPPORTED;
   return WAVE_OK;
+}
+
+// Ratio r of the automatic k = r ||psi|| / ||f_adj|| (the stand-in for the
+// calibration of Sec. 4.1: the smallest k at which FP32 still agrees with
+// FP64).  Defaults: 1e-2 for Algorithm 1 in the velocity form; 5e-2 in the
+// density form, whose FP32 cancellation in K(u^s,u^s) - K(u,u) is larger; 1
+// for the +-k mean, which has no k^2 term to keep small.
+static double default_ratio(const wave_model_s* m, const wave_gradient_opts* o) {
+  if (o->k_ratio > 0.0) return o->k_ratio;
+  if (o->mode == WAVE_SYMMETRIC_K) return 1.0;
+  return m->d.physics == WAVE_DENSITY ? 5e-2 : 1e-2;
 }
 
 static double objective_weight(const wave_gradient_opts* o, const wave_shot& sh) {
@@ -662,7 +750,7 @@ static void carve_batched(Carve& c, const wave_model_s* m, const wave_shot* shot
     w->recp[s] = c.take<int64_t>(std::max(1, shots[s].nrec));
   }
   w->parts = c.take<double>(1024);
-  w->scal = c.take<double>(4);
+  w->scal = c.take<double>(8);
 }
 
 // Exact mode: the forward history u^0..u^{N+1} of one shot at a time.
@@ -693,7 +781,7 @@ static void carve_exact(Carve& c, const wave_model_s* m, const wave_shot* shots,
   w->resid = c.take<float>(maxres);
   w->recp = c.take<int64_t>(maxrec);
   w->parts = c.take<double>(1024);
-  w->scal = c.take<double>(4);
+  w->scal = c.take<double>(8);
 }
 
 extern "C" wave_status wave_gradient_workspace_size(wave_model m, const wave_shot* shots, int32_t nshots,
@@ -718,6 +806,39 @@ extern "C" wave_status wave_gradient_workspace_size(wave_model m, const wave_sho
   return WAVE_OK;
 }
 
+
+// Final scaling into grad_dev with the FP64 2-norm of the result (Sec. 4's
+// K~, or the exact gradient), and the call's scalars for the metrics.
+static wave_status finish_call(const wave_model_s* m, const float* acc, const double* kd, double inv_dt,
+                               int superposition, bool chain_v, float* grad_dev, double* parts, double* scal,
+                               const double* misfit_acc, double* grad_norm_dev, cudaStream_t s) {
+  const Geom& g = m->g;
+  CUDA_TRY(launch_finish(g, acc, kd, inv_dt, superposition, chain_v, m->param, grad_dev, parts, s));
+  CUDA_TRY(launch_sum_final(parts, finish_parts(g.nx * g.ny * g.nz), 1.0, 0, scal + 4, s, grad_norm_dev));
+  if (m->met.on) {
+    CUDA_TRY(cudaMemcpyAsync(scal + 6, misfit_acc, sizeof(double), cudaMemcpyDeviceToDevice, s));
+    CUDA_TRY(mark(m, kEvAdjointEnd, s));
+  }
+  return WAVE_OK;
+}
+
+// Reset the metrics of the model for a new gradient call.
+static cudaError_t metrics_begin(const wave_model_s* m, const wave_shot* shots, int32_t nshots, int mode,
+                                 const double* scal) {
+  auto& M = m->met;
+  M.valid = M.on;
+  if (!M.on) return cudaSuccess;
+  M.used = 0;
+  M.bytes = 0.0;
+  M.launches = 0;
+  M.units = 0.0;
+  const double cells = (double)(m->g.nx * m->g.ny * m->g.nz);
+  for (int i = 0; i < nshots; ++i) M.units += cells * shots[i].nt;
+  M.scal = scal;
+  M.mode = mode;
+  return cudaSuccess;
+}
+
 // Standard adjoint over the stored forward history (Sec. 2.2 sensitivity
 // analysis): forward with every level kept, then the adjoint recursion
 // lambda^{j-1} = 2 lambda^j - lambda^{j+1} + dt^2/a (L lambda^j + f_adj^j) from
@@ -726,7 +847,7 @@ extern "C" wave_status wave_gradient_workspace_size(wave_model m, const wave_sho
 // result; memory grows with N.
 static wave_status gradient_exact(wave_model m, const wave_shot* shots, int32_t nshots,
                                   const wave_gradient_opts* opts, float* grad_dev, double* misfit_dev,
-                                  double* k_dev, void* ws, cudaStream_t s) {
+                                  double* k_dev, double* norm_dev, void* ws, cudaStream_t s) {
   const Geom& g = m->g;
   const double dt = m->d.dt;
   Carve c(ws);
@@ -737,11 +858,13 @@ static wave_status gradient_exact(wave_model m, const wave_shot* shots, int32_t 
   CUDA_TRY(cudaMemsetAsync(w.acc, 0, g.cells * sizeof(float), s));
   CUDA_TRY(cudaMemsetAsync(misfit_acc, 0, sizeof(double), s));
   CUDA_TRY(launch_set_k(kd, 1.0, s));  // the adjoint source enters unscaled
+  CUDA_TRY(metrics_begin(m, shots, nshots, opts->mode, w.scal));
   auto level = [&](int n) { return w.hist + (size_t)n * g.cells; };
   for (int si = 0; si < nshots; ++si) {
     const wave_shot& sh = shots[si];
     const int N = sh.nt;
     const double wgt = objective_weight(opts, sh);
+    CUDA_TRY(mark(m, kEvStart, s));
     CUDA_TRY(launch_pitch_indices(g, sh.rec_cells_dev, sh.nrec, w.recp, s));
     CUDA_TRY(cudaMemsetAsync(level(0), 0, 2 * g.cells * sizeof(float), s));
     SparseArgs gat = sparse_args(m, w.recp, sh.nrec);
@@ -777,6 +900,7 @@ static wave_status gradient_exact(wave_model m, const wave_shot* shots, int32_t 
       CUDA_TRY(launch_sumsq_partial(w.resid, nullptr, nres, w.parts, np, s));
       CUDA_TRY(launch_sum_final(w.parts, np, 0.5 * wgt * dt, 1, misfit_acc, s));
     }
+    CUDA_TRY(mark(m, kEvForwardEnd, s));
     // adjoint: lambda^{N+1} = lambda^N = 0
     CUDA_TRY(cudaMemsetAsync(w.lam0, 0, g.cells * sizeof(float), s));
     CUDA_TRY(cudaMemsetAsync(w.lam1, 0, g.cells * sizeof(float), s));
@@ -799,15 +923,19 @@ static wave_status gradient_exact(wave_model m, const wave_shot* shots, int32_t 
       CUDA_TRY(run_step(m, a, s));
       std::swap(lam_cur, lam_next);  // lam_cur = lambda^{j-1}
     }
+    if (si + 1 < nshots) CUDA_TRY(mark(m, kEvAdjointEnd, s));
   }
-  CUDA_TRY(launch_finish(g, w.acc, kd, 1.0 / dt, 0, opts->grad_wrt == WAVE_GRAD_PARAM, m->param, grad_dev, s));
+  CUDA_TRY(cudaMemsetAsync(kd, 0, sizeof(double), s));   // no k in this mode
+  wave_status st = finish_call(m, w.acc, kd, 1.0 / dt, 0, opts->grad_wrt == WAVE_GRAD_PARAM, grad_dev, w.parts,
+                               w.scal, misfit_acc, norm_dev, s);
+  if (st != WAVE_OK) return st;
   if (k_dev) CUDA_TRY(cudaMemsetAsync(k_dev, 0, sizeof(double), s));
   return WAVE_OK;
 }
 
 static wave_status gradient_batched(wave_model m, const wave_shot* shots, int32_t nshots,
                                     const wave_gradient_opts* opts, float* grad_dev, double* misfit_dev,
-                                    double* k_dev, void* ws, cudaStream_t s) {
+                                    double* k_dev, double* norm_dev, void* ws, cudaStream_t s) {
   const Geom& g = m->g;
   const double dt = m->d.dt;
   Carve c(ws);
@@ -815,12 +943,14 @@ static wave_status gradient_batched(wave_model m, const wave_shot* shots, int32_
   carve_batched(c, m, shots, nshots, &w);
   double* kd = w.scal + 0;
   double* misfit_acc = misfit_dev ? misfit_dev : w.scal + 3;
+  CUDA_TRY(metrics_begin(m, shots, nshots, opts->mode, w.scal));
+  CUDA_TRY(mark(m, kEvStart, s));
   CUDA_TRY(cudaMemsetAsync(w.acc, 0, g.cells * sizeof(float), s));
   if (w.comp) CUDA_TRY(cudaMemsetAsync(w.comp, 0, g.cells * sizeof(float), s));
   CUDA_TRY(cudaMemsetAsync(misfit_acc, 0, sizeof(double), s));
   const bool auto_k = !(opts->k > 0.0);
   if (!auto_k) CUDA_TRY(launch_set_k(kd, opts->k, s));
-  const double ratio = opts->k_ratio > 0.0 ? opts->k_ratio : 1e-2;
+  const double ratio = default_ratio(m, opts);
   std::vector<void*> prev(nshots), cur(nshots);
   std::vector<SparseArgs> sp(nshots);
   int nmax = 0;
@@ -910,6 +1040,7 @@ static wave_status gradient_batched(wave_model m, const wave_shot* shots, int32_
     }
     CUDA_TRY(launch_auto_k(w.scal + 1, w.scal + 2, ratio, objective_weight(opts, sh), kd, s));
   }
+  CUDA_TRY(mark(m, kEvForwardEnd, s));
   // ---- superposed pass: shot s runs j = N_s..1 at global steps t = j --------
   std::vector<void*> us_cur(nshots), us_next(nshots);
   std::vector<SparseArgs> sb(nshots);
@@ -953,7 +1084,9 @@ static wave_status gradient_batched(wave_model m, const wave_shot* shots, int32_
       std::swap(us_cur[si], us_next[si]);
     }
   }
-  CUDA_TRY(launch_finish(g, w.acc, kd, 1.0 / dt, 1, opts->grad_wrt == WAVE_GRAD_PARAM, m->param, grad_dev, s));
+  wave_status st = finish_call(m, w.acc, kd, 1.0 / dt, 1, opts->grad_wrt == WAVE_GRAD_PARAM, grad_dev, w.parts,
+                               w.scal, misfit_acc, norm_dev, s);
+  if (st != WAVE_OK) return st;
   if (k_dev) CUDA_TRY(cudaMemcpyAsync(k_dev, kd, sizeof(double), cudaMemcpyDeviceToDevice, s));
   return WAVE_OK;
 }
@@ -961,8 +1094,8 @@ static wave_status gradient_batched(wave_model m, const wave_shot* shots, int32_
 
 extern "C" wave_status wave_adjoint_sensitivity(wave_model m, const wave_shot* shots, int32_t nshots,
                                                 const wave_gradient_opts* opts, float* grad_dev,
-                                                double* misfit_dev, double* k_dev, void* ws, size_t ws_bytes,
-                                                void* stream) {
+                                                double* misfit_dev, double* k_dev, double* grad_norm_dev,
+                                                void* ws, size_t ws_bytes, void* stream) {
   if (!m || !grad_dev) return WAVE_EINVAL;
   wave_status st = validate_shots(m, shots, nshots, false);
   if (st != WAVE_OK) return st;
@@ -973,8 +1106,9 @@ extern "C" wave_status wave_adjoint_sensitivity(wave_model m, const wave_shot* s
   wave_gradient_workspace_size(m, shots, nshots, opts, &need);
   if (!ws || ws_bytes < need || reinterpret_cast<uintptr_t>(ws) % 256) return WAVE_EWORKSPACE;
   cudaStream_t s = (cudaStream_t)stream;
-  if (opts->mode == WAVE_EXACT_STORED) return gradient_exact(m, shots, nshots, opts, grad_dev, misfit_dev, k_dev, ws, s);
-  if (opts->batched) return gradient_batched(m, shots, nshots, opts, grad_dev, misfit_dev, k_dev, ws, s);
+  if (opts->mode == WAVE_EXACT_STORED)
+    return gradient_exact(m, shots, nshots, opts, grad_dev, misfit_dev, k_dev, grad_norm_dev, ws, s);
+  if (opts->batched) return gradient_batched(m, shots, nshots, opts, grad_dev, misfit_dev, k_dev, grad_norm_dev, ws, s);
   const Geom& g = m->g;
   const int stor = m->d.storage;
   const size_t eb = storage_bytes(stor);
@@ -986,6 +1120,7 @@ extern "C" wave_status wave_adjoint_sensitivity(wave_model m, const wave_shot* s
   double* misfit_acc = misfit_dev ? misfit_dev : w.scal + 3;
   const bool sym = opts->mode == WAVE_SYMMETRIC_K;
   const bool rev = opts->mode == WAVE_EXACT_REVERSE;
+  CUDA_TRY(metrics_begin(m, shots, nshots, opts->mode, w.scal));
 
   CUDA_TRY(cudaMemsetAsync(w.acc, 0, g.cells * sizeof(float), s));
   if (w.comp) CUDA_TRY(cudaMemsetAsync(w.comp, 0, g.cells * sizeof(float), s));
@@ -993,7 +1128,7 @@ extern "C" wave_status wave_adjoint_sensitivity(wave_model m, const wave_shot* s
   const bool auto_k = !rev && !(opts->k > 0.0);
   if (rev) CUDA_TRY(launch_set_k(kd, 1.0, s));  // the adjoint source enters unscaled
   else if (!auto_k) CUDA_TRY(launch_set_k(kd, opts->k, s));
-  const double ratio = opts->k_ratio > 0.0 ? opts->k_ratio : (sym ? 1.0 : 1e-2);
+  const double ratio = default_ratio(m, opts);
   // both fields of WAVE_SYMMETRIC_K advance in one launch where the batched kernel applies
   const bool fuse2 = sym && m->d.ndim == 3 && m->d.physics == WAVE_VELOCITY && stor == WAVE_F32;
 
@@ -1001,6 +1136,8 @@ extern "C" wave_status wave_adjoint_sensitivity(wave_model m, const wave_shot* s
     const wave_shot& sh = shots[si];
     const int N = sh.nt;
     const double wgt = objective_weight(opts, sh);
+    if (si > 0) CUDA_TRY(mark(m, kEvAdjointEnd, s));
+    CUDA_TRY(mark(m, kEvStart, s));
     CUDA_TRY(launch_pitch_indices(g, sh.rec_cells_dev, sh.nrec, w.recp, s));
     CUDA_TRY(cudaMemsetAsync(w.u0, 0, g.cells * eb, s));
     CUDA_TRY(cudaMemsetAsync(w.u1, 0, g.cells * eb, s));
@@ -1060,6 +1197,7 @@ extern "C" wave_status wave_adjoint_sensitivity(wave_model m, const wave_shot* s
       }
       CUDA_TRY(launch_auto_k(w.scal + 1, w.scal + 2, ratio, wgt, kd, s));
     }
+    CUDA_TRY(mark(m, kEvForwardEnd, s));
     // prev holds u^N, cur holds u^{N+1}
     if (rev) {
       // ---- u backward by time reversal beside lambda (Eq. kernel1 mixed term)
@@ -1199,9 +1337,53 @@ extern "C" wave_status wave_adjoint_sensitivity(wave_model m, const wave_shot* s
   // ---- K~ = (K(u^s,u^s) - K(u,u)) / 2k (Eq. superposedkernel); the
   // symmetric pair divides by 4k, the reverse-time mode by nothing ----------
   const bool chain_v = opts->grad_wrt == WAVE_GRAD_PARAM && m->d.physics == WAVE_VELOCITY;
-  CUDA_TRY(launch_finish(g, w.acc, kd, (sym ? 0.5 : 1.0) / dt, rev ? 0 : 1, chain_v, m->param, grad_dev, s));
+  if (rev) CUDA_TRY(cudaMemsetAsync(kd, 0, sizeof(double), s));   // no k in this mode
+  wave_status fst = finish_call(m, w.acc, kd, (sym ? 0.5 : 1.0) / dt, rev ? 0 : 1, chain_v, grad_dev, w.parts,
+                                w.scal, misfit_acc, grad_norm_dev, s);
+  if (fst != WAVE_OK) return fst;
   if (k_dev && rev) CUDA_TRY(cudaMemsetAsync(k_dev, 0, sizeof(double), s));
   else if (k_dev) CUDA_TRY(cudaMemcpyAsync(k_dev, kd, sizeof(double), cudaMemcpyDeviceToDevice, s));
+  return WAVE_OK;
+}
+
+// ---------------------------------------------------------------------------
+// per-call metrics
+// ---------------------------------------------------------------------------
+extern "C" wave_status wave_model_set_metrics(wave_model m, int32_t on) {
+  if (!m) return WAVE_EINVAL;
+  m->met.on = on != 0;
+  m->met.valid = false;
+  return WAVE_OK;
+}
+
+extern "C" wave_status wave_gradient_metrics_read(wave_model m, wave_gradient_metrics* out) {
+  if (!m || !out) return WAVE_EINVAL;
+  auto& M = m->met;
+  if (!M.on || !M.valid || M.used == 0 || !M.scal) return WAVE_EINVAL;
+  CUDA_TRY(cudaEventSynchronize(M.ev[M.used - 1]));
+  double sc[8];
+  CUDA_TRY(cudaMemcpy(sc, M.scal, sizeof(sc), cudaMemcpyDeviceToHost));
+  memset(out, 0, sizeof(*out));
+  out->misfit = sc[6];
+  out->k = sc[0];
+  out->grad_l2 = sqrt(sc[4]);
+  double fwd = 0.0, adj = 0.0;
+  for (size_t i = 1; i < M.used; ++i) {
+    float ms = 0.f;
+    CUDA_TRY(cudaEventElapsedTime(&ms, M.ev[i - 1], M.ev[i]));
+    if (M.kind[i] == kEvForwardEnd) fwd += ms;
+    else if (M.kind[i] == kEvAdjointEnd) adj += ms;
+  }
+  float total = 0.f;
+  CUDA_TRY(cudaEventElapsedTime(&total, M.ev[0], M.ev[M.used - 1]));
+  out->forward_ms = fwd;
+  out->adjoint_ms = adj;
+  out->total_ms = total;
+  out->step_bytes = M.bytes;
+  out->cell_updates = M.units;
+  out->step_launches = (int64_t)M.launches;
+  // the optional end-of-call check for non-finite results
+  if (!isfinite(out->misfit) || !isfinite(out->grad_l2) || !isfinite(out->k)) return WAVE_ENONFINITE;
   return WAVE_OK;
 }
 

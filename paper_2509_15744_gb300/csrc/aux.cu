@@ -7,12 +7,30 @@
 // and the source time functions (Eq. source2 and the Ricker wavelet).
 #include <atomic>
 #include <math.h>
+#include <mutex>
+#include <set>
+#include <utility>
 
 #include "wave_internal.cuh"
 
 namespace wave {
 
 static std::atomic<uint64_t> g_launches{0};
+
+// Dynamic shared-memory limit of a kernel, set once per device (the attribute
+// is per device; setting it again while the kernel runs is not allowed).
+cudaError_t set_smem_limit_once(const void* func, int bytes) {
+  static std::mutex mu;
+  static std::set<std::pair<int, const void*>> done;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lock(mu);
+  if (done.count({dev, func})) return cudaSuccess;
+  e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess) done.insert({dev, func});
+  return e;
+}
 void count_launch(int n) { g_launches.fetch_add((uint64_t)n, std::memory_order_relaxed); }
 uint64_t launches() { return g_launches.load(std::memory_order_relaxed); }
 
@@ -78,6 +96,11 @@ cudaError_t launch_coef_density(const Geom& g, const float* gamma, double dt2_ov
 // Neumann).  Leapfrog is stable while it is <= 4.
 __device__ __forceinline__ float hmean(float a, float b) { return 2.f * a * b / (a + b); }
 
+// max that keeps a NaN (fmaxf drops it), so a NaN parameter reaches the check
+__device__ __forceinline__ float max_keep_nan(float a, float b) {
+  return (a != a || b != b) ? __int_as_float(0x7fffffff) : fmaxf(a, b);
+}
+
 __global__ void stability_kernel(Geom g, int physics, float sym, const float* __restrict__ coef,
                                  const float* __restrict__ b, float* __restrict__ partial) {
   __shared__ float red[256];
@@ -104,12 +127,12 @@ __global__ void stability_kernel(Geom g, int physics, float sym, const float* __
       }
       val = 2.f * coef[i] * s;
     }
-    m = fmaxf(m, val);
+    m = max_keep_nan(m, val);
   }
   red[threadIdx.x] = m;
   __syncthreads();
   for (int w = blockDim.x / 2; w > 0; w >>= 1) {
-    if (threadIdx.x < w) red[threadIdx.x] = fmaxf(red[threadIdx.x], red[threadIdx.x + w]);
+    if (threadIdx.x < w) red[threadIdx.x] = max_keep_nan(red[threadIdx.x], red[threadIdx.x + w]);
     __syncthreads();
   }
   if (threadIdx.x == 0) partial[blockIdx.x] = red[0];
@@ -118,11 +141,11 @@ __global__ void stability_kernel(Geom g, int physics, float sym, const float* __
 __global__ void max_final_kernel(const float* __restrict__ partial, int n, float* out) {
   __shared__ float red[256];
   float m = 0.f;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) m = fmaxf(m, partial[i]);
+  for (int i = threadIdx.x; i < n; i += blockDim.x) m = max_keep_nan(m, partial[i]);
   red[threadIdx.x] = m;
   __syncthreads();
   for (int w = blockDim.x / 2; w > 0; w >>= 1) {
-    if (threadIdx.x < w) red[threadIdx.x] = fmaxf(red[threadIdx.x], red[threadIdx.x + w]);
+    if (threadIdx.x < w) red[threadIdx.x] = max_keep_nan(red[threadIdx.x], red[threadIdx.x + w]);
     __syncthreads();
   }
   if (threadIdx.x == 0) out[0] = red[0];
@@ -284,12 +307,16 @@ __global__ void sumsq_partial_kernel(const float* __restrict__ x, const float* _
 }
 
 __global__ void sum_final_kernel(const double* __restrict__ partial, int n, double scale, int accumulate,
-                                 double* out) {
+                                 double* out, double* root) {
   __shared__ double red[32];
   double acc = 0.0;
   for (int i = threadIdx.x; i < n; i += blockDim.x) acc += partial[i];
   const double s = block_sum(acc, red);
-  if (threadIdx.x == 0) out[0] = accumulate ? out[0] + scale * s : scale * s;
+  if (threadIdx.x == 0) {
+    const double v = accumulate ? out[0] + scale * s : scale * s;
+    out[0] = v;
+    if (root) root[0] = sqrt(v);
+  }
 }
 
 cudaError_t launch_sumsq_partial(const float* x, const float* y, int64_t count, double* partial, int nparts,
@@ -300,8 +327,8 @@ cudaError_t launch_sumsq_partial(const float* x, const float* y, int64_t count, 
 }
 
 cudaError_t launch_sum_final(const double* partial, int nparts, double scale, int accumulate, double* out,
-                             cudaStream_t s) {
-  sum_final_kernel<<<1, 256, 0, s>>>(partial, nparts, scale, accumulate, out);
+                             cudaStream_t s, double* root) {
+  sum_final_kernel<<<1, 256, 0, s>>>(partial, nparts, scale, accumulate, out, root);
   count_launch();
   return cudaGetLastError();
 }
@@ -331,13 +358,23 @@ cudaError_t launch_auto_k(const double* psi2, const double* e2, double ratio, do
   return cudaGetLastError();
 }
 
-// ---- finish: K~ = acc / (2 k dt) (or acc / dt for the exact mode) --------
+// ---- finish: K~ = acc / (2 k dt) (or acc / dt for the exact mode), with the
+// per-block FP64 partial sums of K~^2 for the norm (fixed grid, fixed order) --
+int finish_parts(int64_t cells) {
+  int64_t b = (cells + 255) / 256;
+  if (b > 1024) b = 1024;
+  if (b < 1) b = 1;
+  return (int)b;
+}
+
 __global__ void finish_kernel(Geom g, const float* __restrict__ acc, const double* k_dev, double inv_dt,
                               int superposition, int chain_v, const float* __restrict__ param,
-                              float* __restrict__ grad) {
+                              float* __restrict__ grad, double* __restrict__ partial) {
+  __shared__ double red[32];
   const double sc = superposition ? inv_dt / (2.0 * k_dev[0]) : inv_dt;
   const float s = (float)sc;
   const int64_t total = g.nx * g.ny * g.nz;
+  double ss = 0.0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
        i += (int64_t)gridDim.x * blockDim.x) {
     float v = acc[(i / g.nx) * g.px + (i % g.nx)] * s;
@@ -346,13 +383,16 @@ __global__ void finish_kernel(Geom g, const float* __restrict__ acc, const doubl
       v *= -2.f / (p * p * p);   // dC/dv = dC/dm * dm/dv, m = 1/v^2
     }
     grad[i] = v;
+    ss = fma((double)v, (double)v, ss);
   }
+  const double bs = block_sum(ss, red);
+  if (threadIdx.x == 0) partial[blockIdx.x] = bs;
 }
 
 cudaError_t launch_finish(const Geom& g, const float* acc, const double* k_dev, double inv_dt, int superposition,
-                          int chain_v, const float* param, float* grad, cudaStream_t s) {
-  finish_kernel<<<grid_for(g.nx * g.ny * g.nz, 256), 256, 0, s>>>(g, acc, k_dev, inv_dt, superposition, chain_v,
-                                                                    param, grad);
+                          int chain_v, const float* param, float* grad, double* partial, cudaStream_t s) {
+  finish_kernel<<<finish_parts(g.nx * g.ny * g.nz), 256, 0, s>>>(g, acc, k_dev, inv_dt, superposition, chain_v,
+                                                                  param, grad, partial);
   count_launch();
   return cudaGetLastError();
 }

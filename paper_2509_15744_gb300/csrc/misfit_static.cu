@@ -17,9 +17,13 @@
 // first kernel writes every partial sum that the second kernel reads.
 //
 // The first call on a device looks up the array's device address with
-// cudaGetSymbolAddress (with that device current) and caches it; make that
-// first call before any stream capture begins.  The call itself never
-// allocates: no cudaMalloc, cudaFree or allocating library routine.
+// cudaGetSymbolAddress (with that device current) and caches it together with
+// the device's current context; a later call in another context (after a
+// device reset) looks it up again.  Make the first call on a device before
+// any stream capture begins.  The call itself never allocates: no
+// cudaMalloc, cudaFree or allocating library routine.
+#include <cuda.h>   // CUcontext (cuCtxGetCurrent is looked up at run time)
+
 #include <mutex>
 
 #include "wave_internal.cuh"
@@ -37,6 +41,25 @@ static __device__ __align__(256) double g_misfit_partials[kStaticParts];
 
 std::mutex g_addr_mutex;
 double* g_addr[kMaxDevices] = {nullptr};
+CUcontext g_ctx[kMaxDevices] = {nullptr};   // context the cached address belongs to
+
+typedef CUresult (*CtxGetCurrent)(CUcontext*);
+
+// The calling thread's current context (null if it cannot be read).
+CUcontext current_context() {
+  static CtxGetCurrent fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<CtxGetCurrent>(p);
+  });
+  CUcontext c = nullptr;
+  if (fn) fn(&c);
+  return c;
+}
 
 __device__ __forceinline__ double block_reduce(double v, double* red) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
@@ -76,18 +99,21 @@ chunk_final_kernel(const double* __restrict__ partials, int nparts, double scale
   if (threadIdx.x == 0) out[0] = scale * s;
 }
 
-// Device address of the static array on the current device (looked up once).
+// Device address of the static array on the current device: looked up once
+// per device and context.
 cudaError_t scratch_address(double** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
   std::lock_guard<std::mutex> lock(g_addr_mutex);
-  if (g_addr[dev] == nullptr) {
+  const CUcontext ctx = current_context();
+  if (g_addr[dev] == nullptr || ctx == nullptr || ctx != g_ctx[dev]) {
     void* p = nullptr;
     e = cudaGetSymbolAddress(&p, g_misfit_partials);
     if (e != cudaSuccess) return e;
     g_addr[dev] = static_cast<double*>(p);
+    g_ctx[dev] = current_context();   // the lookup may have made the primary context current
   }
   *out = g_addr[dev];
   return cudaSuccess;
@@ -102,16 +128,27 @@ extern "C" wave_status wave_misfit_static(const float* syn_dev, const float* obs
   if (count > (int64_t)kStaticParts * kChunk) return WAVE_EINVAL;  // beyond the static scratch
   double* partials = nullptr;
   cudaError_t e = scratch_address(&partials);
-  if (e != cudaSuccess) return WAVE_ECUDA;
+  if (e != cudaSuccess) {
+    wave::set_last_error("cudaGetSymbolAddress (static misfit scratch)", e);
+    return WAVE_ECUDA;
+  }
   cudaStream_t s = (cudaStream_t)stream;
   const int nparts = (int)((count + kChunk - 1) / kChunk);
   if (nparts > 0) {
     chunk_partial_kernel<<<nparts, kThreads, 0, s>>>(syn_dev, obs_dev, count, partials);
     wave::count_launch();
-    if (cudaGetLastError() != cudaSuccess) return WAVE_ECUDA;
+    e = cudaGetLastError();
+    if (e != cudaSuccess) {
+      wave::set_last_error("chunk_partial_kernel launch", e);
+      return WAVE_ECUDA;
+    }
   }
   chunk_final_kernel<<<1, kThreads, 0, s>>>(partials, nparts, 0.5 * weight * dt, out_dev);
   wave::count_launch();
-  if (cudaGetLastError() != cudaSuccess) return WAVE_ECUDA;
+  e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    wave::set_last_error("chunk_final_kernel launch", e);
+    return WAVE_ECUDA;
+  }
   return WAVE_OK;
 }

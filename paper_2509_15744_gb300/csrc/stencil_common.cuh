@@ -92,10 +92,13 @@ __device__ __forceinline__ float4 mask_row_padding(float4 u, int64_t xl, int64_t
   return u;
 }
 
+// Compensated sum acc += v.  The explicitly rounded operations keep the
+// compiler from fusing the caller's product into v - comp, so every kernel
+// rounds the update the same way.
 __device__ __forceinline__ void kahan_add(float& acc, float& comp, float v) {
-  const float y = v - comp;
-  const float t = acc + y;
-  comp = (t - acc) - y;
+  const float y = __fsub_rn(v, comp);
+  const float t = __fadd_rn(acc, y);
+  comp = __fsub_rn(__fsub_rn(t, acc), y);
   acc = t;
 }
 

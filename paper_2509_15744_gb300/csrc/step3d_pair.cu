@@ -321,13 +321,8 @@ step3d_velocity_pair_kernel(BatchArgs b) {
 template <int R, int TY, int DX, int ACC>
 cudaError_t launch_p(const BatchArgs& b, cudaStream_t s) {
   using PT = PTile<R, TY, DX>;
-  static bool configured = false;
-  if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(step3d_velocity_pair_kernel<R, TY, DX, ACC>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PT::bytes());
-    if (e != cudaSuccess) return e;
-    configured = true;
-  }
+  cudaError_t e = set_smem_limit_once(reinterpret_cast<const void*>(step3d_velocity_pair_kernel<R, TY, DX, ACC>), (int)PT::bytes());
+  if (e != cudaSuccess) return e;
   const Geom& g = b.base.g;
   dim3 grid((unsigned)((g.nz + b.base.zblock - 1) / b.base.zblock), (unsigned)((g.nx + kStrip - 1) / kStrip),
             (unsigned)((g.ny + TY - 1) / TY));

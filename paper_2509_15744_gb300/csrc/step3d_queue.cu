@@ -305,13 +305,8 @@ step3d_velocity_queue_kernel(BatchArgs b) {
 template <int R, int TY, int DX>
 cudaError_t launch_q(const BatchArgs& b, cudaStream_t s) {
   using QT = QTile<R, TY, DX>;
-  static bool configured = false;
-  if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(step3d_velocity_queue_kernel<R, TY, DX>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)QT::bytes());
-    if (e != cudaSuccess) return e;
-    configured = true;
-  }
+  cudaError_t e = set_smem_limit_once(reinterpret_cast<const void*>(step3d_velocity_queue_kernel<R, TY, DX>), (int)QT::bytes());
+  if (e != cudaSuccess) return e;
   const Geom& g = b.base.g;
   dim3 grid((unsigned)((g.nz + b.base.zblock - 1) / b.base.zblock), (unsigned)((g.nx + kStrip - 1) / kStrip),
             (unsigned)((g.ny + TY - 1) / TY));

@@ -246,13 +246,8 @@ step3d_velocity_ring_kernel(BatchArgs b) {
 template <int R, int TY, int D>
 static cudaError_t launch_ring(const BatchArgs& a, cudaStream_t s) {
   using RG = Ring<R, TY, D>;
-  static bool configured = false;
-  if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(step3d_velocity_ring_kernel<R, TY, D>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RG::bytes());
-    if (e != cudaSuccess) return e;
-    configured = true;
-  }
+  cudaError_t e = set_smem_limit_once(reinterpret_cast<const void*>(step3d_velocity_ring_kernel<R, TY, D>), (int)RG::bytes());
+  if (e != cudaSuccess) return e;
   const Geom& g = a.base.g;
   dim3 grid((unsigned)((g.nz + a.base.zblock - 1) / a.base.zblock), (unsigned)((g.nx + kStrip - 1) / kStrip),
             (unsigned)((g.ny + TY - 1) / TY));
@@ -269,16 +264,20 @@ static cudaError_t launch_ring_r(const BatchArgs& a, cudaStream_t s) {
 }
 
 cudaError_t launch_step3d_batched(const BatchArgs& b, int order, cudaStream_t s) {
-  // the fused (u, lambda) pair of the exact reverse-time mode runs only in the pair kernel
+  // Pipelines: 0 this cp.async ring (64-bit offsets: any grid, the fallback);
+  // 3 register queue in z; 4 two fields per pass; 5 two fields per pass with
+  // TMA tensor tiles.  A launch of one field goes to the register queue from
+  // pipelines 3-5.  Pipeline 5 takes every launch of two or more fields it
+  // supports.
+  if (b.base.pipeline == 5 && b.nshots >= 2 && stream_supported(b)) return launch_step3d_stream(b, order, s);
+  // the fused (u, lambda) pair of the exact reverse-time mode runs only in the pair kernels
   if (b.pair_mix) return b.nshots == 2 && b.base.g.plane < (int64_t)1 << 31 ? launch_step3d_pair(b, order, s)
                                                                            : cudaErrorInvalidValue;
-  if (b.base.pipeline == 1) return launch_step3d_tma(b, order, s);
   // pipeline 4 pairs the fields of a launch; a launch of one field gains nothing from it
-  if (b.base.pipeline == 4 && b.nshots >= 2 && b.base.g.plane < (int64_t)1 << 31 && !b.base.mix_a &&
+  if (b.base.pipeline >= 4 && b.nshots >= 2 && b.base.g.plane < (int64_t)1 << 31 && !b.base.mix_a &&
       !b.base.u_out)
     return launch_step3d_pair(b, order, s);
   if (b.base.pipeline >= 3 && b.base.g.plane < (int64_t)1 << 31) return launch_step3d_queue(b, order, s);
-  if (b.base.pipeline == 2 && b.base.g.plane < (int64_t)1 << 31) return launch_step3d_ring2(b, order, s);
   switch (order) {
     case 2: return launch_ring_r<1>(b, s);
     case 4: return launch_ring_r<2>(b, s);

@@ -133,8 +133,8 @@ struct StepArgs {
   int64_t zblock;        // cells of the march axis per CTA (3D) / warp (2D)
   int tile_rows;         // 3D ring kernel: rows per CTA (8 or 16)
   int ring_depth;        // 3D ring kernel: planes copied ahead (2 or 3)
-  int pipeline;          // 3D FP32: 0 cp.async ring, 1 TMA bulk-copy pipeline, 2 cp.async ring with two planes per barrier
-  int* err;              // device error word (TMA pipeline)
+  int pipeline;          // 3D FP32: 0 cp.async ring, 3 register queue, 4 two fields per pass, 5 the same with TMA tiles
+  int* err;              // device error word (bounded waits)
   long long wait_limit_cycles;
   int debug_stall;
   // Exact (stored-history) mode, FP32 velocity only:
@@ -159,16 +159,16 @@ struct BatchArgs {
   float accf[kMaxBatch];         // per-shot factor on acc_scale this step (0: no increment)
   int pair_mix;                  // two fields (u, lambda) in the two-shots-per-pass kernel:
                                  // acc += acc_scale accf[1] (lambda - lambda_new)(u - u_new)
-  // TMA pipeline only:
+  // TMA-tiled pipeline only:
   int* err;                      // set to 1 when a bounded wait gives up
   long long wait_limit_cycles;   // bound of every wait (clock64 cycles)
   int debug_stall;               // test only: issue no copies, so the first wait runs out
 };
 cudaError_t launch_step3d_batched(const BatchArgs& b, int order, cudaStream_t s);
-cudaError_t launch_step3d_tma(const BatchArgs& b, int order, cudaStream_t s);
-cudaError_t launch_step3d_ring2(const BatchArgs& b, int order, cudaStream_t s);
 cudaError_t launch_step3d_queue(const BatchArgs& b, int order, cudaStream_t s);
 cudaError_t launch_step3d_pair(const BatchArgs& b, int order, cudaStream_t s);
+cudaError_t launch_step3d_stream(const BatchArgs& b, int order, cudaStream_t s);
+bool stream_supported(const BatchArgs& b);
 
 
 // ---- sparse (source / receiver) kernel -----------------------------------
@@ -207,14 +207,22 @@ cudaError_t launch_pitch_indices(const Geom& g, const int64_t* flat, int32_t n, 
 cudaError_t launch_dense_to_pitched(const Geom& g, const float* dense, void* pitched, int storage, cudaStream_t s);
 cudaError_t launch_pitched_to_dense(const Geom& g, const void* pitched, float* dense, int storage, cudaStream_t s);
 cudaError_t launch_sumsq_partial(const float* x, const float* y, int64_t count, double* partial, int nparts, cudaStream_t s);
-cudaError_t launch_sum_final(const double* partial, int nparts, double scale, int accumulate, double* out, cudaStream_t s);
+// out = scale * sum (+ out if accumulate); root, if not null, receives sqrt(out).
+cudaError_t launch_sum_final(const double* partial, int nparts, double scale, int accumulate, double* out, cudaStream_t s,
+                             double* root = nullptr);
 cudaError_t launch_set_k(double* k_dev, double k, cudaStream_t s);
 cudaError_t launch_auto_k(const double* psi2, const double* e2, double ratio, double w, double* k_dev, cudaStream_t s);
+// Writes grad and finish_parts(cells) FP64 partial sums of grad^2 to partial.
 cudaError_t launch_finish(const Geom& g, const float* acc, const double* k_dev, double inv_dt, int superposition,
-                          int chain_v, const float* param, float* grad, cudaStream_t s);
+                          int chain_v, const float* param, float* grad, double* partial, cudaStream_t s);
+int finish_parts(int64_t cells);
 cudaError_t launch_wavelet(int kind, double f, int nc, double psi0, double dt, int nt, float* out, cudaStream_t s);
 
 int reduce_parts(int64_t count);   // number of partial sums used for `count` samples
+// Raises a kernel's dynamic shared-memory limit once per device.
+cudaError_t set_smem_limit_once(const void* func, int bytes);
+// Records the text wave_last_error() returns for a failed CUDA call.
+void set_last_error(const char* what, cudaError_t e);
 void count_launch(int n = 1);
 
 }  // namespace wave

@@ -4,7 +4,7 @@ The tiling (`wave_model_set_tiling`: z-block depth, rows per CTA, ring
 depth, pipeline) changes speed only, never results.  `tune()` times a short forward
 pass of the given shots with each candidate (CUDA events inside libwave,
 `wave_timing_*`), keeps the fastest, applies it to the model and caches it
-under a key of (dims, shape, order, physics, storage, shots per launch).
+under a key of (dims, shape, order, physics, storage, Kahan, shots per launch).
 """
 from __future__ import annotations
 
@@ -19,21 +19,28 @@ from . import wave as W
 CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "tune_cache.json")
 
 
-def candidates(ndim: int, nz: int):
+def candidates(ndim: int, nz: int, batched: bool = False):
+    """Tilings worth timing: in 2D the rows per warp; in 3D the register-queue
+    kernel (pipeline 3) for one field per launch, and for batched launches also
+    the two-shots-per-pass kernels (4: cp.async staging; 5: TMA tensor tiles,
+    z-block fixed at 8)."""
     if ndim == 2:
         return [(zb, 8, 3, 0) for zb in (8, 16, 32, 64, 128) if zb <= max(8, nz)]
     out = []
-    for pipe in (0, 1, 2, 3, 4):
-        for rows in ((8,) if pipe == 2 else (16,) if pipe == 4 else (8, 16)):
-            for depth in (2, 3):
-                for zb in (16, 32, 64, 128):
-                    if zb <= max(16, nz):
-                        out.append((zb, rows, depth, pipe))
+    for rows in (8, 16):
+        for depth in (2, 3):
+            for zb in (32, 64, 128):
+                if zb <= max(32, nz):
+                    out.append((zb, rows, depth, 3))
+    if batched:
+        out += [(zb, 16, 2, 4) for zb in (32, 64, 128) if zb <= max(32, nz)]
+        out += [(8, 16, 2, 5), (8, 16, 3, 5)]
     return out
 
 
 def _key(model: W.Model, batch: int) -> str:
-    return json.dumps([len(model.shape), list(model.shape), model.order, model.physics, model.storage, batch])
+    return json.dumps([len(model.shape), list(model.shape), model.order, model.physics, model.storage,
+                       bool(model.kahan), batch])
 
 
 def _load() -> Dict[str, list]:
@@ -70,7 +77,7 @@ def tune(model: W.Model, shots: Sequence[W.Shot], steps: int = 12, batched: bool
                             None if s.observed is None else s.observed[:, :n + 1].contiguous()))
     nz = model.shape[0]
     results = []
-    for cand in candidates(len(model.shape), nz):
+    for cand in candidates(len(model.shape), nz, batched and batch > 1):
         model.set_tiling(*cand)
         model.gradient(probe, batched=batched, k=1.0)          # warm-up (and attribute setup)
         torch.cuda.synchronize(dev)

@@ -76,6 +76,7 @@ _model_set_block = _sig("wave_model_set_block", _st, _vp, C.c_int64)
 _model_get_block = _sig("wave_model_get_block", _st, _vp, C.POINTER(C.c_int64))
 _model_set_tiling = _sig("wave_model_set_tiling", _st, _vp, C.c_int64, _i32, _i32, _i32)
 _model_check = _sig("wave_model_check", _st, _vp, _vp)
+_model_set_param = _sig("wave_model_set_param", _st, _vp, _vp, _vp)
 _model_set_debug = _sig("wave_model_set_debug", _st, _vp, _i32, C.c_int64)
 _model_pitch = _sig("wave_model_pitch", _st, _vp, C.POINTER(C.c_int64))
 _step = _sig("wave_step", _st, _vp, _i32, C.POINTER(_vp), C.POINTER(_vp), C.POINTER(C.c_float), _vp, _vp, _vp)
@@ -84,7 +85,17 @@ _forward = _sig("wave_forward", _st, _vp, C.POINTER(ShotDesc), _i32, _vp, _vp, _
 _grad_ws = _sig("wave_gradient_workspace_size", _st, _vp, C.POINTER(ShotDesc), _i32, C.POINTER(GradOpts),
                 C.POINTER(_sz))
 _adjoint_sensitivity = _sig("wave_adjoint_sensitivity", _st, _vp, C.POINTER(ShotDesc), _i32, C.POINTER(GradOpts),
-                            _vp, _vp, _vp, _vp, _sz, _vp)
+                            _vp, _vp, _vp, _vp, _vp, _sz, _vp)
+
+
+class GradMetrics(C.Structure):
+    _fields_ = [("misfit", C.c_double), ("k", C.c_double), ("grad_l2", C.c_double), ("forward_ms", C.c_double),
+                ("adjoint_ms", C.c_double), ("total_ms", C.c_double), ("step_bytes", C.c_double),
+                ("cell_updates", C.c_double), ("step_launches", C.c_int64)]
+
+
+_set_metrics = _sig("wave_model_set_metrics", _st, _vp, _i32)
+_metrics_read = _sig("wave_gradient_metrics_read", _st, _vp, C.POINTER(GradMetrics))
 _timing_enable = _sig("wave_timing_enable", _st, _i32)
 _timing_read = _sig("wave_timing_read", _st, C.POINTER(C.c_double), C.POINTER(C.c_uint64), C.POINTER(C.c_double))
 _misfit_scratch = _sig("wave_misfit_scratch_size", _sz, C.c_int64)
@@ -244,6 +255,7 @@ class Model:
         self._h = h_
         self._fws = None
         self._gws = None
+        self.grad_norm = None   # device FP64 ||grad||_2 of the last gradient call
 
     def __del__(self):
         h = getattr(self, "_h", None)
@@ -265,9 +277,31 @@ class Model:
         _check(_model_set_tiling(self._h, int(zblock), int(tile_rows), int(ring_depth), int(pipeline)),
                "wave_model_set_tiling")
 
+    def set_metrics(self, on: bool = True):
+        """Record per-pass CUDA events in later gradient calls (wave_model_set_metrics)."""
+        _check(_set_metrics(self._h, int(bool(on))), "wave_model_set_metrics")
+
+    def metrics(self) -> dict:
+        """Figures of the last gradient call (waits for it): misfit, k, grad_l2,
+        forward_ms, adjoint_ms, total_ms, step_bytes, cell_updates,
+        step_launches.  Raises WaveError(WAVE_ENONFINITE) on a NaN/Inf result."""
+        m = GradMetrics()
+        _check(_metrics_read(self._h, C.byref(m)), "wave_gradient_metrics_read")
+        return {n: getattr(m, n) for n, _ in GradMetrics._fields_}
+
     def check(self, stream=None) -> int:
-        """Wait for the stream; WAVE_ETIMEOUT (5) if a bounded device wait gave up."""
+        """Wait for the stream; WAVE_ETIMEOUT (5) if a bounded device wait gave up,
+        WAVE_EUNSTABLE (2) / WAVE_ENONFINITE (6) for an unstable or non-finite
+        parameter of the last set_param."""
         return int(_model_check(self._h, _stream(stream)))
+
+    def set_param(self, param: torch.Tensor, stream=None):
+        """Replace the parameter grid (same shape) without a host wait; check()
+        reports an unstable or non-finite value."""
+        if not param.is_cuda or param.dtype != torch.float32 or tuple(param.shape) != self.shape:
+            raise TypeError("param must be a CUDA float32 tensor of the model's shape")
+        self.param = param.contiguous()
+        _check(_model_set_param(self._h, _ptr(self.param), _stream(stream)), "wave_model_set_param")
 
     def set_debug(self, stall_pipeline: bool, wait_limit_cycles: int = 4_000_000_000):
         _check(_model_set_debug(self._h, int(bool(stall_pipeline)), int(wait_limit_cycles)), "wave_model_set_debug")
@@ -335,7 +369,8 @@ class Model:
     def gradient(self, shots: Sequence[Shot], objective: str = "l2", k: Optional[float] = None,
                  k_ratio: Optional[float] = None, mode: str = "superposition", batched: bool = False,
                  grad_wrt: str = "mass", patch_sign: float = 1.0, stream=None, out: Optional[torch.Tensor] = None):
-        """Algorithm 1.  Returns (grad [*shape] float32, misfit [1] float64, k [1] float64).
+        """Algorithm 1.  Returns (grad [*shape] float32, misfit [1] float64, k [1] float64);
+        self.grad_norm receives ||grad||_2 (FP64 device reduction, [1] float64).
 
         mode: "superposition" (Algorithm 1), "exact" (adjoint over the stored
         forward history), "symmetric" (mean of the +k and -k superposition
@@ -355,6 +390,8 @@ class Model:
         grad = out if out is not None else torch.empty(self.shape, dtype=torch.float32, device=dev)
         mis = torch.empty(1, dtype=torch.float64, device=dev)
         kd = torch.empty(1, dtype=torch.float64, device=dev)
+        norm = torch.empty(1, dtype=torch.float64, device=dev)
         _check(_adjoint_sensitivity(self._h, arr, len(shots), C.byref(o), _ptr(grad), _ptr(mis), _ptr(kd),
-                                    _ptr(ws), ws.numel(), _stream(stream)), "wave_adjoint_sensitivity")
+                                    _ptr(norm), _ptr(ws), ws.numel(), _stream(stream)), "wave_adjoint_sensitivity")
+        self.grad_norm = norm
         return grad, mis, kd

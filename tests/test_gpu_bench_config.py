@@ -1,0 +1,85 @@
+"""Parity of the configuration bench.py times, on a crop the oracle can run.
+
+bench.py's default workload is the 3D multi-shot case: 512^3, 8th order,
+Dirichlet, layered velocity, 16 shots on a 4x4 source grid with record
+lengths drawn from 1500..2500 steps, receivers on every second surface cell,
+Ricker 15 Hz, automatic k at the default ratio, one batched launch per global
+step on the TMA-streamed two-shots-per-pass kernel.  Here the same generator builds that
+workload on a 32^3 grid with the SAME record lengths and shot layout (256
+receivers), and the summed K~ of the batched call is compared element-wise
+with the sum of the oracle's per-shot Algorithm 1 results at the k the GPU
+used (bar 1e-3 relative L2; misfit 2e-4, twice the 1e-4 trace bar since C
+is quadratic in the traces; automatic k 1e-4 against the oracle's rule).  The observed data are the oracle's FP64 forward traces of
+the true model.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2509_15744_gb300 import workloads as WL
+
+from _oracle_pool import adjoint_source_of, forward_traces, pool, superposition
+from _problems import rel_l2
+
+pytestmark = pytest.mark.gpu
+
+SHAPE = (32, 32, 32)
+
+
+@pytest.fixture(scope="module")
+def W():
+    import __graft_entry__ as ge
+    ge.build()
+    from paper_2509_15744_gb300 import wave
+    return wave
+
+
+@pytest.fixture(scope="module")
+def case():
+    wl = WL.workload2(shape=SHAPE)
+    dt = O.cfl_dt(wl.h, wl.vmax, 3, wl.order, wl.cfl_fraction)
+    true_spec = ("velocity", np.asarray(wl.true_param, np.float64), wl.h, dt, wl.order, wl.bc)
+    init_spec = ("velocity", np.asarray(wl.init_param, np.float64), wl.h, dt, wl.order, wl.bc)
+    wavs = [O.ricker(np.arange(n + 1) * dt, wl.wavelet.freq) for n in wl.nt]
+    with pool() as p:
+        obs = p.map(forward_traces, [(true_spec, wl.sources[i], wavs[i], wl.receivers[i], wl.nt[i])
+                                     for i in range(wl.nshots)])
+        fadj0 = p.apply(adjoint_source_of, ((init_spec, wl.sources[0], wavs[0], wl.receivers[0], wl.nt[0],
+                                             obs[0], 1.0),))
+    k_rule = O.auto_k(O.Shot(wl.sources[0], wavs[0], wl.receivers[0], obs[0], 1.0), fadj0, wl.nt[0], 1e-2)
+    return dict(wl=wl, dt=dt, init_spec=init_spec, wavs=wavs, obs=obs, k_rule=k_rule)
+
+
+def _gpu_gradient(W, case, kahan, tiling):
+    import torch
+    wl, dt = case["wl"], case["dt"]
+    dev = torch.device("cuda")
+    m = W.Model(torch.from_numpy(np.ascontiguousarray(wl.init_param, np.float32)).to(dev), wl.h, dt, wl.order,
+                "velocity", "dirichlet", kahan=kahan)
+    m.set_tiling(*tiling)
+    shots = [W.Shot(wl.sources[i], W.wavelet("ricker", wl.wavelet.freq, dt, wl.nt[i], device=dev),
+                    torch.from_numpy(wl.receivers[i]).to(dev),
+                    torch.from_numpy(case["obs"][i].astype(np.float32)).to(dev)) for i in range(wl.nshots)]
+    g, c, k = m.gradient(shots, batched=True)
+    torch.cuda.synchronize()
+    return g.cpu().numpy().astype(np.float64), float(c.item()), float(k.item())
+
+
+@pytest.mark.parametrize("kahan", [False, True])
+def test_benchmarked_batched_configuration_matches_oracle(W, case, kahan):
+    wl = case["wl"]
+    g, c, k = _gpu_gradient(W, case, kahan, (8, 16, 2, 5))
+    assert abs(k - case["k_rule"]) <= 1e-4 * case["k_rule"]
+    jobs = [(case["init_spec"], wl.sources[i], case["wavs"][i], wl.receivers[i], wl.nt[i],
+             case["obs"][i], 1.0, k) for i in range(wl.nshots)]
+    with pool() as p:
+        parts = p.map(superposition, jobs)
+    ref = sum(kt for kt, _ in parts)
+    c_ref = sum(ci for _, ci in parts)
+    e = rel_l2(g, ref)
+    ec = abs(c - c_ref) / abs(c_ref)
+    print(f"\nbench configuration on {SHAPE}, 16 shots, N {min(wl.nt)}..{max(wl.nt)}, kahan={kahan}: "
+          f"K~ rel L2 {e:.2e}, misfit rel {ec:.2e}, k {k:.4e}")
+    # traces match to 1e-4 (the wavefield bar); C is quadratic in them: 2e-4
+    assert ec <= 2e-4
+    assert e <= 1e-3

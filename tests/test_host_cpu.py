@@ -15,15 +15,28 @@ def test_tuner_candidates_respect_pipeline_constraints():
     pytest.importorskip("torch")
     from paper_2509_15744_gb300 import tune
     c3 = tune.candidates(3, 512)
-    pipes = {c[3] for c in c3}
-    assert pipes == {0, 1, 2, 3, 4}
-    assert all(c[1] == 8 for c in c3 if c[3] == 2)      # two planes per barrier: 8 rows
-    assert all(c[1] == 16 for c in c3 if c[3] == 4)     # two shots per pass: 16 rows
-    assert all(c[2] in (2, 3) and c[0] in (16, 32, 64, 128) for c in c3)
+    assert {c[3] for c in c3} == {3}                     # one field per launch: register queue
+    cb = tune.candidates(3, 512, batched=True)
+    assert {c[3] for c in cb} == {3, 4, 5}
+    assert all(c[1] == 16 for c in cb if c[3] in (4, 5))   # two shots per pass: 16 rows
+    assert all(c[0] == 8 for c in cb if c[3] == 5)         # TMA-streamed kernel: z-block of 8
+    assert all(c[2] in (2, 3) and c[0] in (8, 32, 64, 128) for c in cb)
     c2 = tune.candidates(2, 300)
     assert all(c[3] == 0 and c[1] == 8 for c in c2)
     # small grids do not get z-blocks deeper than the grid
-    assert all(c[0] <= 16 for c in tune.candidates(3, 12))
+    assert all(c[0] <= 32 for c in tune.candidates(3, 12))
+
+
+def test_tuner_cache_key_separates_kahan():
+    pytest.importorskip("torch")
+    from paper_2509_15744_gb300 import tune
+
+    class M:
+        shape, order, physics, storage = (64, 64, 64), 8, "velocity", "f32"
+
+    a, b = M(), M()
+    a.kahan, b.kahan = False, True
+    assert tune._key(a, 16) != tune._key(b, 16)
 
 
 def test_traffic_record_is_used_only_for_the_current_kernel_source(tmp_path, monkeypatch):

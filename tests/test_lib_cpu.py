@@ -130,3 +130,38 @@ def test_plain_c_client_links_and_runs_the_host_checks(lib, tmp_path):
     r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=120)
     assert r.returncode == 0, r.stdout + r.stderr
     assert "ok" in r.stdout
+
+
+def test_workspace_checks_happen_before_any_device_work(lib):
+    # An undersized or misaligned caller workspace is refused on the host
+    # (WAVE_EWORKSPACE = 3) before anything touches the GPU; the pointers are
+    # never dereferenced, so fake addresses serve.
+    from paper_2509_15744_gb300 import wave as W
+    d = W.GridDesc()
+    d.ndim, d.order = 3, 8
+    d.n[0], d.n[1], d.n[2] = 130, 20, 21
+    d.h, d.dt = 10.0, W.cfl_dt(3, 8, 10.0, 4500.0, 0.5)
+    need = C.c_size_t(0)
+    assert W._model_ws(C.byref(d), C.byref(need)) == 0
+    param = C.c_void_p(0x10000)
+    h = C.c_void_p()
+    aligned = C.c_void_p(0x7f0000000000)
+    assert W._model_create(C.byref(d), param, C.c_void_p(0x7f0000000000 + 8), need.value, None,
+                           C.byref(h)) == 3                  # not 256-byte aligned
+    assert W._model_create(C.byref(d), param, aligned, need.value - 1, None, C.byref(h)) == 3   # one byte short
+    assert not h.value
+    # misfit: scratch smaller than wave_misfit_scratch_size(count), or misaligned
+    n = 1 << 20
+    small = W._misfit_scratch(n) - 8
+    out = C.c_void_p(0x20000)
+    assert W._misfit(C.c_void_p(0x30000), None, n, 1.0, 1.0, out, aligned, small, None) == 3
+    assert W._misfit(C.c_void_p(0x30000), None, n, 1.0, 1.0, out, C.c_void_p(0x7f0000000004),
+                     W._misfit_scratch(n), None) == 3
+
+
+def test_metrics_calls_validate_on_the_host(lib):
+    from paper_2509_15744_gb300 import wave as W
+    m = W.GradMetrics()
+    assert W._metrics_read(None, C.byref(m)) == 1
+    assert W._set_metrics(None, 1) == 1
+    assert W._model_set_param(None, None, None) == 1

@@ -456,6 +456,25 @@ def test_misfit_hand_example():
     assert O.misfit(tr, None, 0.5, O.patch_weight(4, 1.0)) == 0.5 * 0.5 * 0.5 * 30.0
 
 
+def test_auto_k_hand_example():
+    """The automatic k (reading R9): k = r ||psi|| / ||f_adj|| over levels 1..N
+    of the first shot, worked by hand.  Level 0 of both series is excluded
+    (f^0 is never used and u^0 = 0 gives no adjoint source)."""
+    # psi levels 1..3 = (2, 1, 2): ||psi|| = 3; f_adj levels 1..3 of two
+    # receivers = (0, 4, 0) and (0, 0, 3): ||f_adj|| = 5.  Level-0 entries (7,
+    # 100, 11) would change the result if they were counted.
+    wav = np.array([7.0, 2.0, 1.0, 2.0])
+    f_adj = np.array([[100.0, 0.0, 4.0, 0.0], [11.0, 0.0, 0.0, 3.0]])
+    shot = O.Shot(0, wav, np.array([1, 2]))
+    assert O.auto_k(shot, f_adj, 3, 1e-2) == pytest.approx(1e-2 * 3.0 / 5.0, rel=1e-15)
+    assert O.auto_k(shot, f_adj, 3, 0.5) == pytest.approx(0.5 * 0.6, rel=1e-15)
+    # only levels up to N enter: with N = 2 the last column drops out,
+    # ||psi|| = sqrt(5), ||f_adj|| = 4
+    assert O.auto_k(shot, f_adj, 2, 1.0) == pytest.approx(math.sqrt(5.0) / 4.0, rel=1e-15)
+    # a zero residual has no scale: k = 1
+    assert O.auto_k(shot, np.zeros_like(f_adj), 3, 1e-2) == 1.0
+
+
 # ---------------------------------------------------------------------------
 # Planted mistakes: each must be caught by a pin above
 # ---------------------------------------------------------------------------
