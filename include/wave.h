@@ -208,9 +208,11 @@ wave_status wave_model_get_block(wave_model model, int64_t* zblock);
  * with one CTA barrier per plane (64-bit offsets: any grid size); 3: z
  * neighbours in a register queue, one cp.async-staged plane tile per plane;
  * 4: two fields of a batched launch per pass, lower z neighbours in
- * registers and upper ones from the staged tiles, 16 rows only; 5: as 4 with
- * the tiles copied by TMA tensor copies into an mbarrier ring over z-blocks
- * of 8 planes (zblock ignored), 16 rows only -- the default.  Pipelines 3-5
+ * registers and upper ones from the staged tiles, 16 rows only -- the
+ * default; 5: the fields of a batched launch one after the other over
+ * z-blocks of 8 planes (zblock ignored) with the accumulator of the block in
+ * registers across them, the tiles copied by TMA tensor copies into an
+ * mbarrier ring that holds one field's tiles, 16 rows only.  Pipelines 3-5
  * send a launch of one field to the register-queue kernel.  Speed only;
  * results are identical. */
 wave_status wave_model_set_tiling(wave_model model, int64_t zblock, int32_t tile_rows, int32_t ring_depth,

@@ -19,18 +19,25 @@ uint64_t launches();
 }
 
 static thread_local std::string g_last_error;
+static thread_local std::string g_inner_error;   // the failing call inside a launcher, if it said
 
 void wave::set_last_error(const char* what, cudaError_t e) {
   g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
 }
 
-#define CUDA_TRY(expr)                                            \
-  do {                                                            \
-    cudaError_t _e = (expr);                                      \
-    if (_e != cudaSuccess) {                                      \
-      g_last_error = std::string(#expr) + ": " + cudaGetErrorString(_e); \
-      return WAVE_ECUDA;                                          \
-    }                                                             \
+void wave::note_error(const char* what, cudaError_t e) {
+  g_inner_error = std::string(what) + ": " + cudaGetErrorString(e);
+}
+
+#define CUDA_TRY(expr)                                                            \
+  do {                                                                            \
+    g_inner_error.clear();                                                        \
+    cudaError_t _e = (expr);                                                      \
+    if (_e != cudaSuccess) {                                                      \
+      g_last_error = std::string(#expr) + ": " + cudaGetErrorString(_e);          \
+      if (!g_inner_error.empty()) g_last_error += " (in " + g_inner_error + ")"; \
+      return WAVE_ECUDA;                                                          \
+    }                                                                             \
   } while (0)
 
 // ---------------------------------------------------------------------------
@@ -106,6 +113,17 @@ struct wave_model_s {
   mutable Metrics met;
 };
 
+// Records a timing event on s.  While s is being captured into a CUDA graph
+// the event is recorded as an external event node, so every replay records
+// it; outside capture that flag is not allowed and a plain record is used.
+static cudaError_t record_event(cudaEvent_t e, cudaStream_t s) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaError_t err = cudaStreamIsCapturing(s, &cs);
+  if (err != cudaSuccess) return err;
+  return cs == cudaStreamCaptureStatusActive ? cudaEventRecordWithFlags(e, s, cudaEventRecordExternal)
+                                             : cudaEventRecord(e, s);
+}
+
 enum { kEvStart = 0, kEvForwardEnd = 1, kEvAdjointEnd = 2 };
 
 // Record a pass boundary of the current gradient call (metrics on only).
@@ -120,7 +138,7 @@ static cudaError_t mark(const wave_model_s* m, int kind, cudaStream_t s) {
   }
   if (M.kind.size() <= M.used) M.kind.resize(M.used + 1);
   M.kind[M.used] = kind;
-  return cudaEventRecord(M.ev[M.used++], s);
+  return record_event(M.ev[M.used++], s);
 }
 
 static wave_status validate_desc(const wave_grid_desc* d) {
@@ -261,10 +279,11 @@ wave_status wave_model_create(const wave_grid_desc* desc, const float* param_dev
   m->bmat = bmat;
   m->zblock = default_zblock(g);
   // untuned default: one field per launch on the register-queue kernel, two
-  // or more on the TMA-tiled two-fields-per-pass kernel
+  // or more on the two-shots-per-pass kernel (the faster of the batched ones
+  // on every measured workload)
   m->tile_rows = 16;
   m->ring_depth = 2;
-  m->pipeline = 5;
+  m->pipeline = 4;
   m->err = errw;
   m->part = part;
   m->maxv = maxv;
@@ -407,6 +426,7 @@ struct StepTiming {
 };
 static StepTiming g_timing;
 
+
 static double step_bytes(const wave_model_s* m, const StepArgs& a) {
   const double cells = (double)(m->g.nx * m->g.ny * m->g.nz);
   const double eb = (double)storage_bytes(m->d.storage);
@@ -428,12 +448,14 @@ static cudaError_t run_step(const wave_model_s* m, const StepArgs& a, cudaStream
     e0 = g_timing.ev[g_timing.used];
     e1 = g_timing.ev[g_timing.used + 1];
     g_timing.used += 2;
-    cudaEventRecordWithFlags(e0, s, cudaEventRecordExternal);
+    cudaError_t err = record_event(e0, s);
+    if (err != cudaSuccess) return err;
   }
   cudaError_t err = m->d.physics == WAVE_VELOCITY ? launch_step_velocity(a, m->d.order, m->d.storage, s)
                                                   : launch_step_density(a, m->d.storage, s);
+  if (err != cudaSuccess) return err;
   if (g_timing.on) {
-    cudaEventRecordWithFlags(e1, s, cudaEventRecordExternal);
+    err = record_event(e1, s);
     g_timing.bytes += step_bytes(m, a);
     g_timing.launches += 1;
   }
@@ -456,16 +478,18 @@ static cudaError_t run_batched(const wave_model_s* m, const BatchArgs& b, cudaSt
     e0 = g_timing.ev[g_timing.used];
     e1 = g_timing.ev[g_timing.used + 1];
     g_timing.used += 2;
-    cudaEventRecordWithFlags(e0, s, cudaEventRecordExternal);
+    cudaError_t err = record_event(e0, s);
+    if (err != cudaSuccess) return err;
   }
   cudaError_t err = launch_step3d_batched(b, m->d.order, s);
+  if (err != cudaSuccess) return err;
   const double cells = (double)(m->g.nx * m->g.ny * m->g.nz);
   bool any = false;
   for (int i = 0; i < b.nshots; ++i) any |= b.accf[i] != 0;
   // per shot: read u^n, u^{n-1}, write u^{n+1}; once: coef, acc (+comp) RMW
   const double bytes = cells * (12.0 * b.nshots + 4.0 + (any ? (b.base.comp ? 16.0 : 8.0) : 0.0));
   if (g_timing.on) {
-    cudaEventRecordWithFlags(e1, s, cudaEventRecordExternal);
+    err = record_event(e1, s);
     g_timing.bytes += bytes;
     g_timing.launches += 1;
   }

@@ -24,11 +24,15 @@ cudaError_t set_smem_limit_once(const void* func, int bytes) {
   static std::set<std::pair<int, const void*>> done;
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return e;
+  if (e != cudaSuccess) {
+    note_error("cudaGetDevice", e);
+    return e;
+  }
   std::lock_guard<std::mutex> lock(mu);
   if (done.count({dev, func})) return cudaSuccess;
   e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
   if (e == cudaSuccess) done.insert({dev, func});
+  else note_error("cudaFuncSetAttribute(max dynamic shared memory)", e);
   return e;
 }
 void count_launch(int n) { g_launches.fetch_add((uint64_t)n, std::memory_order_relaxed); }

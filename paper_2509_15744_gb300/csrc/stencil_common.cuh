@@ -78,6 +78,32 @@ __device__ __forceinline__ void x_terms(const float* srow, int lane, float lap[4
   }
 }
 
+// The same x part from the three float4 A (cells x-4..x-1), B (x..x+3) and
+// C (x+4..x+7) already in registers, with the same operation order.
+template <int R>
+__device__ __forceinline__ void x_terms_abc(const float4& A, const float4& B, const float4& C, float lap[4],
+                                            float ndim_c0) {
+  const float e[12] = {A.x, A.y, A.z, A.w, B.x, B.y, B.z, B.w, C.x, C.y, C.z, C.w};
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    float s = ndim_c0 * e[4 + i];
+#pragma unroll
+    for (int j = 1; j <= R; ++j) s = fmaf(cw<R>(j), e[4 + i + j] + e[4 + i - j], s);
+    lap[i] = s;
+  }
+}
+
+// x ghosts of a row whose ends fall on float4 boundaries (nx a multiple of
+// 128): the four cells beyond the left end (A of lane 0) and beyond the right
+// end (C of lane 31) from the lane's own cells B by the boundary rule.
+// Dirichlet: u_{-1} = 0, u_{-1-j} = -u_{j-1}; Neumann: u_{-1-j} = u_j.
+__device__ __forceinline__ float4 left_ghosts(const float4& B, int bc) {
+  return bc == WAVE_NEUMANN ? make_float4(B.w, B.z, B.y, B.x) : make_float4(-B.z, -B.y, -B.x, 0.f);
+}
+__device__ __forceinline__ float4 right_ghosts(const float4& B, int bc) {
+  return bc == WAVE_NEUMANN ? make_float4(B.w, B.z, B.y, B.x) : make_float4(0.f, -B.w, -B.z, -B.y);
+}
+
 // In the shared-memory ring kernels the lane's own float4 is read from the
 // staged row, whose cells at x >= nx hold mirrored ghost values; zeroing them
 // there (u = u_old = coef = 0 in the row padding) keeps the padding at zero

@@ -75,6 +75,7 @@ step3d_velocity_pair_kernel(BatchArgs b) {
   const int64_t xl = x0 + 4 * lane;
   const bool row_valid = y < g.ny;
   const bool xfix = (x0 == 0) || (x0 + kStrip + R > g.nx);
+  const bool xfast = (g.nx % kStrip) == 0;   // row ends on strip boundaries: x ghosts in registers
   const int row_off = (int)(y * g.px + xl);
   const int own = (R + warp) * kRowW + 4 + 4 * lane;   // own cells in a tile
   const uint32_t smem0 = (uint32_t)__cvta_generic_to_shared(tiles);
@@ -209,28 +210,34 @@ step3d_velocity_pair_kernel(BatchArgs b) {
     // One field f at plane z (buffer bz; lower queue ql): new level un and
     // the centre value u the increment is taken against.
     auto field = [&](int f, int J, int z, int bz_, bool top, const float4 (&ql)[R], const float4& u_old,
-                     float4& u, float4& un) {
+                     const int (&zoff)[R], float4& u, float4& un) {
       float* tile = tiles + (f * NB + bz_) * PT::TILE;
       float* srow = tile + (R + warp) * kRowW;
       u = *reinterpret_cast<const float4*>(tile + own);
-      if (xfix) {
+      float lap[4];
+      if (xfix && !xfast) {   // ragged row end: ghosts written into the staged row
         const float val = (fx_pos >= 0 && fx_sgn != 0.f) ? fx_sgn * srow[fx_src] : 0.f;
         __syncwarp();
         if (fx_pos >= 0) srow[fx_pos] = val;
         __syncwarp();
         u = mask_row_padding(u, xl, g.nx);
+        x_terms<R>(srow, lane, lap, 3.f * cw<R>(0));
+      } else {
+        float4 xa = *reinterpret_cast<const float4*>(srow + 4 * lane);
+        float4 xc = *reinterpret_cast<const float4*>(srow + 8 + 4 * lane);
+        if (xfix) {   // row ends on a strip boundary: ghosts from the lane's own cells
+          if (lane == 0 && x0 == 0) xa = left_ghosts(u, g.bc);
+          if (lane == 31 && x0 + kStrip == g.nx) xc = right_ghosts(u, g.bc);
+        }
+        x_terms_abc<R>(xa, u, xc, lap, 3.f * cw<R>(0));
       }
-      float lap[4];
-      x_terms<R>(srow, lane, lap, 3.f * cw<R>(0));
       float2 l01 = make_float2(lap[0], lap[1]), l23 = make_float2(lap[2], lap[3]);
-      int bj = bz_;
 #pragma unroll
       for (int j = 1; j <= R; ++j) {
-        bj = bj + 1 == NB ? 0 : bj + 1;   // buffer of plane z+j
         const float4 ym = *reinterpret_cast<const float4*>(tile + own - j * kRowW);
         const float4 yp = *reinterpret_cast<const float4*>(tile + own + j * kRowW);
         const float4 zm = ql[(J - j + R) % R];
-        float4 zp = *reinterpret_cast<const float4*>(tiles + (f * NB + bj) * PT::TILE + own);
+        float4 zp = *reinterpret_cast<const float4*>(tiles + f * NB * PT::TILE + zoff[j - 1]);
         if (top) zp = f4_scale(zp, zsign(z + j));   // mirror sign above the domain (wall tile is zero)
         const float2 c2 = make_float2(cw<R>(j), cw<R>(j));
         l01 = __ffma2_rn(c2, __fadd2_rn(__fadd2_rn(make_float2(ym.x, ym.y), make_float2(yp.x, yp.y)),
@@ -276,12 +283,19 @@ step3d_velocity_pair_kernel(BatchArgs b) {
           if (row_valid && z + 1 < z1) load(off + g.plane, n_oa, n_ob, n_cf, n_ac, n_cp);
           if (row_valid) {
             const bool top = z + R >= g.nz;
+            int zoff[R];   // own cells of planes z+1 .. z+r in the tile ring (both fields)
+#pragma unroll
+            for (int j = 1; j <= R; ++j) {
+              int bj = bz + j;
+              bj -= bj >= NB ? NB : 0;
+              zoff[j - 1] = bj * PT::TILE + own;
+            }
             float4 ua, una;
-            field(0, J, z, bz, top, qa, oa, ua, una);
+            field(0, J, z, bz, top, qa, oa, zoff, ua, una);
             *reinterpret_cast<float4*>(upA + off) = una;
             float4 ubv = zero4, unb = zero4;
             if (two) {
-              field(1, J, z, bz, top, qb, ob, ubv, unb);
+              field(1, J, z, bz, top, qb, ob, zoff, ubv, unb);
               *reinterpret_cast<float4*>(upB + off) = unb;
             }
             if (ACC == kPairMix && acc_on) {
@@ -328,7 +342,9 @@ cudaError_t launch_p(const BatchArgs& b, cudaStream_t s) {
             (unsigned)((g.ny + TY - 1) / TY));
   step3d_velocity_pair_kernel<R, TY, DX, ACC><<<grid, TY * 32, PT::bytes(), s>>>(b);
   count_launch();
-  return cudaGetLastError();
+  e = cudaGetLastError();
+  if (e != cudaSuccess) note_error("step kernel launch", e);
+  return e;
 }
 
 template <int R, int DX>

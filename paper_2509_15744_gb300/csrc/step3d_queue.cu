@@ -312,7 +312,9 @@ cudaError_t launch_q(const BatchArgs& b, cudaStream_t s) {
             (unsigned)((g.ny + TY - 1) / TY));
   step3d_velocity_queue_kernel<R, TY, DX><<<grid, TY * 32, QT::bytes(), s>>>(b);
   count_launch();
-  return cudaGetLastError();
+  e = cudaGetLastError();
+  if (e != cudaSuccess) note_error("step kernel launch", e);
+  return e;
 }
 
 template <int R>

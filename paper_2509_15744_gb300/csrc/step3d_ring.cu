@@ -253,7 +253,9 @@ static cudaError_t launch_ring(const BatchArgs& a, cudaStream_t s) {
             (unsigned)((g.ny + TY - 1) / TY));
   step3d_velocity_ring_kernel<R, TY, D><<<grid, TY * 32, RG::bytes(), s>>>(a);
   count_launch();
-  return cudaGetLastError();
+  e = cudaGetLastError();
+  if (e != cudaSuccess) note_error("step kernel launch", e);
+  return e;
 }
 
 template <int R>

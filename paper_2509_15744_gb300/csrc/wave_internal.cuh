@@ -223,6 +223,9 @@ int reduce_parts(int64_t count);   // number of partial sums used for `count` sa
 cudaError_t set_smem_limit_once(const void* func, int bytes);
 // Records the text wave_last_error() returns for a failed CUDA call.
 void set_last_error(const char* what, cudaError_t e);
+// Names the call that failed inside a launcher; the entry point adds it to
+// the text of wave_last_error().
+void note_error(const char* what, cudaError_t e);
 void count_launch(int n = 1);
 
 }  // namespace wave

@@ -97,7 +97,7 @@ def _perturbed_design(n=363, seed=9):
     from scipy.ndimage import gaussian_filter
     rng = np.random.default_rng(seed)
     d = gaussian_filter(rng.standard_normal((n, n)), 6.0)
-    return np.clip(0.5 + d / (4 * d.std()), 0.0, 1.0)
+    return np.clip(0.4 + d / (5 * d.std()), 0.0, 0.8)   # stays below the solid, within the time step's bound
 
 
 def _spec(prob):
@@ -164,12 +164,26 @@ def _study(W, prob):
 
 
 def _band(rows, tol=0.05):
-    """Longest run of consecutive exponents with FP32 error below tol (decades)."""
-    best = cur = 0
-    for r in rows:
-        cur = cur + 1 if r["fp32"] < tol else 0
-        best = max(best, cur)
-    return max(best - 1, 0) if best else -1
+    """Width in decades of the range of k with FP32 error below tol, the
+    crossings located by log-log interpolation between the sampled decades
+    (0 if no sample is below tol)."""
+    e = [r["e"] for r in rows]
+    v = [np.log10(r["fp32"]) for r in rows]
+    t = np.log10(tol)
+    best = 0.0
+    i = 0
+    while i < len(rows):
+        if v[i] >= t:
+            i += 1
+            continue
+        j = i
+        while j + 1 < len(rows) and v[j + 1] < t:
+            j += 1
+        lo = e[i] if i == 0 else e[i - 1] + (v[i - 1] - t) / (v[i - 1] - v[i]) * (e[i] - e[i - 1])
+        hi = e[j] if j == len(rows) - 1 else e[j] + (t - v[j]) / (v[j + 1] - v[j]) * (e[j + 1] - e[j])
+        best = max(best, hi - lo)
+        i = j + 1
+    return best
 
 
 def _check_hockey_stick(rows, min_decades):
@@ -192,7 +206,8 @@ def _check_hockey_stick(rows, min_decades):
 
 def test_fwi_k_study(W, problems):
     rows = _study(W, problems["fwi"])
-    _check_hockey_stick(rows, min_decades=2)
+    print(f"FWI band of k with < 5% error: {_band(rows):.2f} decades")
+    _check_hockey_stick(rows, min_decades=1.5)
 
 
 def test_tato_k_study_with_the_number_of_steps_and_the_design(W, problems):
@@ -200,12 +215,17 @@ def test_tato_k_study_with_the_number_of_steps_and_the_design(W, problems):
     best = {}
     for N in (1200, 1800, 4800, 9600):
         rows = _study(W, problems[f"tato{N}"])
-        _check_hockey_stick(rows, min_decades=2)
+        _check_hockey_stick(rows, min_decades=1.5)
         bands[N], best[N] = _band(rows), min(r["fp32"] for r in rows)
     rows = _study(W, problems["tato_design"])
-    _check_hockey_stick(rows, min_decades=1)
-    print(f"\nTATO bands of k with < 5% error (decades): {bands}, perturbed design: {_band(rows)}")
-    print(f"TATO best FP32 error per N: {best}, perturbed design: {min(r['fp32'] for r in rows):.3e}")
-    # the number of steps shifts the band only a little (Fig. effectsonapproximation)
-    assert max(bands.values()) - min(bands.values()) <= 3
-    assert _band(rows) >= bands[1800] - 3
+    _check_hockey_stick(rows, min_decades=1.0)
+    print(f"\nTATO bands of k with < 5% error (decades): { {n: round(b, 2) for n, b in bands.items()} }, "
+          f"perturbed design: {_band(rows):.2f}")
+    print(f"TATO best FP32 error per N: { {n: float(f'{b:.3e}') for n, b in best.items()} }, "
+          f"perturbed design: {min(r['fp32'] for r in rows):.3e}")
+    # more steps make the approximation somewhat worse, not unusable
+    # (Fig. effectsonapproximation): the best error grows, the band narrows by
+    # less than a decade
+    assert best[9600] >= best[1200]
+    assert bands[1200] - bands[9600] < 1.0
+    assert _band(rows) >= bands[1800] - 1.5

@@ -1,13 +1,16 @@
-"""The TMA-streamed two-shots-per-pass step kernel (tiling pipeline 5).
+"""The TMA-tiled batched step kernel (tiling pipeline 5): the shots of a
+launch one after the other over z-blocks of 8 planes, the accumulator of the
+block in registers across them.
 
 It performs the arithmetic of the other 3D pipelines element by element, so
-its results must be bit-identical to the register-queue and pair kernels,
-which the oracle parity tests pin.  The shapes put CTAs at every kind of edge:
-y boundaries at both ends and interior row tiles (ny = 50), a partial last
-z-block (nz not a multiple of 8), ragged x strips (nx = 261), odd and even
-shot counts (a pass with one field), uneven record lengths, both boundary
-conditions, all four orders, Kahan on and off, and the exact reverse-time
-mode (u and lambda as the two fields of a pass, mixed-term accumulation).
+its results must be bit-identical to the two-shots-per-pass kernel, which the
+oracle parity tests pin.  The shapes put CTAs at every kind of edge: y
+boundaries at both ends and interior row tiles (ny = 50), partial last
+z-blocks (nz not a multiple of 8, one plane in the last block), ragged x
+strips (nx = 261) and strip-aligned rows, odd and even shot counts, uneven
+record lengths, both boundary conditions, all four orders, Kahan on and off;
+the exact reverse-time mode under this tiling (its (u, lambda) launches go to
+the two-shots-per-pass kernel) gives the same result too.
 """
 import numpy as np
 import pytest
