@@ -47,13 +47,23 @@ def parse():
     ap.add_argument("--grad-mode", default="superposition", choices=["superposition", "symmetric", "reverse"],
                     help="gradient: Algorithm 1, the +-k mean, or the two-field reverse-time adjoint "
                          "(the last two are exact and run shot by shot)")
-    ap.add_argument("--kahan", action="store_true")
+    ap.add_argument("--kahan", dest="kahan", action="store_true", default=None,
+                    help="Kahan-compensated sensitivity (default: on for w4, whose configuration names it)")
+    ap.add_argument("--no-kahan", dest="kahan", action="store_false")
     ap.add_argument("--tiling", default=None,
                     help="zblock:rows:depth:pipeline for the 3D step kernel instead of the autotuner's pick")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain-path comparison")
     ap.add_argument("--no-graph", action="store_true", help="time eager calls instead of CUDA-graph replays")
+    ap.add_argument("--storage", default="f32", choices=["f32", "bf16", "f16"],
+                    help="storage type of the resident time levels (stencil arithmetic stays FP32)")
+    ap.add_argument("--compare-exact", action="store_true",
+                    help="after the timed region, the exact discrete gradient (the history-free +-k mean and, "
+                         "where it fits, the stored-history adjoint) as the reference of the timed result")
+    ap.add_argument("--fd-check", action="store_true",
+                    help="after the timed region, a central finite difference of C along a smooth random "
+                         "direction against <grad, direction>")
     ap.add_argument("--refined-data", action="store_true",
                     help="observed data from the true model on a grid twice as fine with twice the steps "
                          "(no inverse crime), generated with the GPU forward")
@@ -356,6 +366,8 @@ def main():
         return
 
     wl = make_workload(args.workload, args.shape, args.shots, args.nt)
+    if args.kahan is None:
+        args.kahan = args.workload == "w4"
     dt = W.cfl_dt(wl.ndim, wl.order, wl.h, wl.vmax, wl.cfl_fraction)
     batched_ok = wl.ndim == 3 and wl.physics == "velocity" and wl.nshots > 1
     mode = args.mode if args.mode != "auto" else ("batched" if batched_ok else "plain")
@@ -393,7 +405,7 @@ def main():
             observed[i] = mtrue.forward([W.Shot(wl.sources[i], wavs[i], recs[i])])[0]
         del mtrue, ptrue
     shots = [W.Shot(wl.sources[i], wavs[i], recs[i], observed[i]) for i in range(wl.nshots)]
-    model = W.Model(param0, wl.h, dt, wl.order, wl.physics, wl.bc, kahan=args.kahan)
+    model = W.Model(param0, wl.h, dt, wl.order, wl.physics, wl.bc, kahan=args.kahan, storage=args.storage)
     gkw = dict(objective=wl.objective, patch_sign=wl.patch_sign, batched=(mode == "batched"), mode=args.grad_mode)
     from paper_2509_15744_gb300 import tune
     if args.tiling:
@@ -495,7 +507,7 @@ def main():
             sh = [W.Shot(wl.sources[i], h_wav[i].to(dev, non_blocking=True), h_rec[i].to(dev, non_blocking=True),
                          h_obs[i].to(dev, non_blocking=True) if h_obs[i] is not None else None)
                   for i in range(wl.nshots)]
-            m2 = W.Model(p, wl.h, dt, wl.order, wl.physics, wl.bc, kahan=args.kahan)
+            m2 = W.Model(p, wl.h, dt, wl.order, wl.physics, wl.bc, kahan=args.kahan, storage=args.storage)
             m2.set_tiling(*tiling)
             g2, mi2, _ = m2.gradient(sh, **gkw)
             h_grad.copy_(g2, non_blocking=True)
@@ -543,21 +555,94 @@ def main():
         sampler.close()
         cpu = {"value": r, "unit": UNIT, "cores": sampler.procs, "kind": "oracle", "sample": sampler.desc}
 
+    # ---- accuracy of the timed result at full size ----------------------------
+    accuracy = None
+    if args.compare_exact or args.fd_check:
+        accuracy = {}
+        gsum = torch.linalg.vector_norm(grad.double()).item()
+        ref_model = model
+        if args.storage != "f32":   # the references are computed with FP32 storage
+            ref_model = W.Model(param0, wl.h, dt, wl.order, wl.physics, wl.bc, kahan=args.kahan)
+            ref_model.set_tiling(*tiling)
+        if args.compare_exact:
+            gs, _, _ = ref_model.gradient(shots, objective=wl.objective, patch_sign=wl.patch_sign, mode="symmetric")
+            barrier()
+            ns = torch.linalg.vector_norm(gs.double()).item()
+            dn = torch.linalg.vector_norm((grad - gs).double()).item()
+            accuracy["exact_symmetric"] = {
+                "rel_l2_of_timed_result": dn / ns if ns > 0 else None,
+                "exact_norm": ns,
+                "what": "exact discrete gradient from the +-k mean (history-free, pinned to the FP64 oracle)"}
+            hist_bytes = (max(wl.nt) + 2) * wl.ncells * 4
+            free, _ = torch.cuda.mem_get_info(dev)
+            if wl.physics == "velocity" and hist_bytes < 0.8 * free:
+                del model._gws
+                model._gws = None
+                a0, b0 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a0.record(stream)
+                ge, _, _ = ref_model.gradient(shots, objective=wl.objective, patch_sign=wl.patch_sign, mode="exact")
+                b0.record(stream)
+                barrier()
+                ne = torch.linalg.vector_norm(ge.double()).item()
+                accuracy["exact_stored"] = {
+                    "rel_l2_of_timed_result": torch.linalg.vector_norm((grad - ge).double()).item() / ne
+                    if ne > 0 else None,
+                    "rel_l2_symmetric_vs_stored": torch.linalg.vector_norm((gs - ge).double()).item() / ne
+                    if ne > 0 else None,
+                    "history_GB": hist_bytes / 1e9,
+                    "Gcell_updates_per_s": units_of(wl) / (a0.elapsed_time(b0) / 1e3) / 1e9,
+                    "what": "standard adjoint over the stored forward history (memory grows with N)"}
+                del ge
+                ref_model._gws = None
+            del gs
+        if args.fd_check:
+            # C(p + e d) - C(p - e d) over 2e against <grad, d>, d smooth and random
+            gen = torch.Generator(device=dev)
+            gen.manual_seed(12)
+            d = torch.randn(param0.shape, generator=gen, device=dev)
+            for _ in range(3):   # smooth by repeated neighbour averaging along every axis
+                for ax in range(d.dim()):
+                    d = (d + torch.roll(d, 1, ax) + torch.roll(d, -1, ax)) / 3
+            if wl.physics == "density":
+                # keep the design below 1: the material interpolation stiffens
+                # steeply towards gamma = 1 and the time step must stay stable
+                d = d * (param0 < 0.9).to(d.dtype)
+            d = d / d.abs().max()
+            eps = (1e-3 if wl.physics == "velocity" else 1e-2) * float(param0.abs().max())
+            cs = []
+            for sgn in (1.0, -1.0):
+                mp = W.Model((param0 + sgn * eps * d).contiguous(), wl.h, dt, wl.order, wl.physics, wl.bc,
+                             kahan=args.kahan)
+                mp.set_tiling(*tiling)
+                _, c_, _ = mp.gradient(shots, objective=wl.objective, patch_sign=wl.patch_sign, mode="symmetric",
+                                       grad_wrt="param")
+                cs.append(float(c_.item()))
+                del mp
+            fd = (cs[0] - cs[1]) / (2 * eps)
+            gp, _, _ = ref_model.gradient(shots, objective=wl.objective, patch_sign=wl.patch_sign, grad_wrt="param")
+            dirv = float((gp.double() * d.double()).sum().item())
+            accuracy["finite_difference"] = {"fd": fd, "directional_derivative": dirv,
+                                             "rel_err": abs(dirv - fd) / max(abs(fd), 1e-300), "eps": eps,
+                                             "what": "central difference of C along a smooth random direction "
+                                                     "vs <dC/dparam of the timed method, direction>"}
+
     if rank == 0:
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "vs_baseline": None, "dtype": "f32" if args.storage == "f32" else f"f32 arithmetic, {args.storage} storage",
+            "data": "synthetic",
             "config": {"workload": wl.name, "shape": list(wl.shape), "order": wl.order, "physics": wl.physics,
                        "shots": wl.nshots, "nt_total": int(sum(wl.nt)),
                        "mode": mode + (", graph replay" if use_graph else ", eager calls"),
                        "gradient": args.grad_mode, "kahan": args.kahan,
-                       "storage": "f32", "parallelism": f"replicas x{world}", "tiling": list(tiling),
+                       "storage": args.storage, "parallelism": f"replicas x{world}", "tiling": list(tiling),
                        "l2": "inputs larger than L2 (each resident grid > 129 MB)",
                        "observed_data": "true model on a 2x grid with 2x steps" if args.refined_data
                        else "true model on the same grid"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "gpu_launches": int(launches),
             "plain": plain, "check": {"misfit": misfit_val, "grad_l2": grad_norm, "k": k_val},
+            "accuracy": accuracy,
         }
         print(json.dumps(out), flush=True)
     if dist is not None:

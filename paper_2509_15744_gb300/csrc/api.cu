@@ -901,17 +901,20 @@ static wave_status gradient_exact(wave_model m, const wave_shot* shots, int32_t 
     gat.gsrc = level(1);
     gat.glevel = 1;
     CUDA_TRY(launch_sparse(gat, WAVE_F32, s));
+    // The step takes the same operations as wave_forward and the other modes
+    // (f^n subtracted from the level the step overwrites, then the in-place
+    // update), so the stored levels, traces and misfit are bitwise those of
+    // the forward: u^{n-1} is copied into the slot of u^{n+1} first.
     SparseArgs inj = sparse_args(m, w.recp, 0);
     inj.src_p = pitched_cell(g, sh.src_cell);
     inj.wavelet = sh.wavelet_dev;
-    inj.inj_sign = 1.f;  // add f^n to the level the step just wrote
     for (int n = 1; n <= N; ++n) {
-      StepArgs a = step_args(m, level(n), level(n - 1));
-      a.u_out = level(n + 1);
-      CUDA_TRY(run_step(m, a, s));
+      CUDA_TRY(cudaMemcpyAsync(level(n + 1), level(n - 1), g.cells * sizeof(float), cudaMemcpyDeviceToDevice, s));
       inj.dst = level(n + 1);
       inj.ilevel = n;
       CUDA_TRY(launch_sparse(inj, WAVE_F32, s));
+      StepArgs a = step_args(m, level(n), level(n + 1));
+      CUDA_TRY(run_step(m, a, s));
       if (n + 1 <= N) {
         gat.gsrc = level(n + 1);
         gat.glevel = n + 1;

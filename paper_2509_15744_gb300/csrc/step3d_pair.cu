@@ -9,8 +9,12 @@
 // * a CTA of 16 warps owns 16 rows x 128 cells and marches up z over a block
 //   of planes, advancing the shots of the launch two at a time; the two
 //   fields share the march: one barrier and one set of index and loop
-//   bookkeeping per plane, one load of coef and one read-modify-write of the
+//   bookkeeping per plane, one load of coef and one update of the
 //   accumulator (both increments) per cell and plane;
+// * with more than two shots and a z-block of at most 32 planes (16 with
+//   Kahan compensation) the accumulator tile stays in tensor memory between
+//   the pairs: read from HBM by the first pair, written back by the last, so
+//   it crosses HBM once per launch instead of once per pair;
 // * per shot, the tile of each plane (own rows + r halo rows, 4 halo cells
 //   per side) is staged by cp.async r+1+depth planes ahead (ring depth 2 or
 //   3 of the tiling) into r+2+depth buffers: the
@@ -40,6 +44,30 @@ __device__ __forceinline__ void pcp_wait() { asm volatile("cp.async.wait_group %
 
 enum { kPairNone = 0, kPairSq = 1, kPairKahan = 2, kPairMix = 3 };
 
+// Tensor memory (TMEM, 128 lanes x 512 columns of 32 bits per SM) holds the
+// accumulator (and Kahan compensation) tile of the CTA's z-block between the
+// shot pairs of a launch.  Warp w reaches lanes 32 (w mod 4) .. +31, one per
+// thread; a thread's 4 cells of plane z - z0 take 4 columns, so the four warps
+// sharing a lane quarter and a z-block of P planes fill 16 P columns:
+// P <= 32 for the accumulator alone, P <= 16 with the compensation beside it
+// (columns 256..511).
+constexpr int kTmemPlanes = 32;
+constexpr int kTmemPlanesKahan = 16;
+__device__ __forceinline__ void tm_ld4(uint32_t ta, float4& v) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];"
+               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "r"(ta) : "memory");
+}
+// wait for the loads; the registers pass through so that no use moves above it
+__device__ __forceinline__ void tm_wait_ld(float4& v, float4& w) {
+  asm volatile("tcgen05.wait::ld.sync.aligned;" : "+f"(v.x), "+f"(v.y), "+f"(v.z), "+f"(v.w),
+               "+f"(w.x), "+f"(w.y), "+f"(w.z), "+f"(w.w) :: "memory");
+}
+__device__ __forceinline__ void tm_st4(uint32_t ta, const float4& v) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1, %2, %3, %4};"
+               :: "r"(ta), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w) : "memory");
+}
+__device__ __forceinline__ void tm_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
 template <int R, int TY, int DX>
 struct PTile {
   static constexpr int D = R + 1 + DX;           // planes staged ahead of the centre plane
@@ -54,7 +82,7 @@ struct PTile {
   static_assert(K <= 32, "chunk masks are 32-bit");
 };
 
-template <int R, int TY, int DX, int ACC>
+template <int R, int TY, int DX, int ACC, bool TM>
 __global__ void __launch_bounds__(TY * 32, 1)
 step3d_velocity_pair_kernel(BatchArgs b) {
   using PT = PTile<R, TY, DX>;
@@ -128,7 +156,26 @@ step3d_velocity_pair_kernel(BatchArgs b) {
   }
   const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
 
+  __shared__ uint32_t tm_slot;
+  uint32_t tm_base = 0;
+  const uint32_t tm_ncols = ACC == kPairKahan ? 512u : (a.zblock * 16 <= 256 ? 256u : 512u);
+  if constexpr (TM) {
+    if (warp == 0) {
+      const uint32_t sa = (uint32_t)__cvta_generic_to_shared(&tm_slot);
+      asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(sa), "r"(tm_ncols)
+                   : "memory");
+      asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    tm_base = tm_slot;
+  }
+  // this warp's TMEM lanes (32 per warp of a group of four) and first column
+  const uint32_t tm_row = tm_base + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)((warp >> 2) * a.zblock * 4);
+
   for (int s0 = 0; s0 < b.nshots; s0 += 2) {
+    const bool first = s0 == 0, last = s0 + 2 >= b.nshots;
     const bool two = s0 + 1 < b.nshots;   // uniform: a second field in this pass
     const float* __restrict__ ucA = b.cur[s0];
     const float* __restrict__ ucB = two ? b.cur[s0 + 1] : b.cur[s0];
@@ -197,7 +244,7 @@ step3d_velocity_pair_kernel(BatchArgs b) {
       uoa = *reinterpret_cast<const float4*>(upA + o);
       if (two) uob = *reinterpret_cast<const float4*>(upB + o);
       c = __ldg(reinterpret_cast<const float4*>(a.coef + o));
-      if (acc_on) {
+      if (TM ? first : acc_on) {
         acv = *reinterpret_cast<const float4*>(a.acc + o);
         if (ACC == kPairKahan) cpv = *reinterpret_cast<const float4*>(a.comp + o);
       }
@@ -282,6 +329,12 @@ step3d_velocity_pair_kernel(BatchArgs b) {
           float4 n_oa = oa, n_ob = ob, n_cf = cf, n_ac = ac, n_cp = cp;
           if (row_valid && z + 1 < z1) load(off + g.plane, n_oa, n_ob, n_cf, n_ac, n_cp);
           if (row_valid) {
+            const bool tm_in = TM && !first && (acc_on || last);
+            const uint32_t tm_a = tm_row + (uint32_t)(4 * (z - z0));
+            if (tm_in) {
+              tm_ld4(tm_a, ac);
+              if (ACC == kPairKahan) tm_ld4(tm_a + 256u, cp);
+            }
             const bool top = z + R >= g.nz;
             int zoff[R];   // own cells of planes z+1 .. z+r in the tile ring (both fields)
 #pragma unroll
@@ -306,6 +359,18 @@ step3d_velocity_pair_kernel(BatchArgs b) {
               ac.z = fmaf(scB * (ubv.z - unb.z), ua.z - una.z, ac.z);
               ac.w = fmaf(scB * (ubv.w - unb.w), ua.w - una.w, ac.w);
               *reinterpret_cast<float4*>(a.acc + off) = ac;
+            } else if (TM) {
+              if (tm_in) tm_wait_ld(ac, cp);
+              if (onA) accumulate(scA, ua, una);
+              if (onB) accumulate(scB, ubv, unb);
+              if (last) {
+                *reinterpret_cast<float4*>(a.acc + off) = ac;
+                if (ACC == kPairKahan) *reinterpret_cast<float4*>(a.comp + off) = cp;
+              } else if (acc_on || first) {
+                tm_st4(tm_a, ac);
+                if (ACC == kPairKahan) tm_st4(tm_a + 256u, cp);
+                tm_wait_st();
+              }
             } else if (acc_on) {
               if (onA) accumulate(scA, ua, una);
               if (onB) accumulate(scB, ubv, unb);
@@ -330,17 +395,25 @@ step3d_velocity_pair_kernel(BatchArgs b) {
     pcp_wait<0>();
     __syncthreads();   // the buffers are refilled for the next pair
   }
+  if constexpr (TM) {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tm_base), "r"(tm_ncols) : "memory");
+    }
+  }
 }
 
-template <int R, int TY, int DX, int ACC>
+template <int R, int TY, int DX, int ACC, bool TM = false>
 cudaError_t launch_p(const BatchArgs& b, cudaStream_t s) {
   using PT = PTile<R, TY, DX>;
-  cudaError_t e = set_smem_limit_once(reinterpret_cast<const void*>(step3d_velocity_pair_kernel<R, TY, DX, ACC>), (int)PT::bytes());
+  cudaError_t e = set_smem_limit_once(reinterpret_cast<const void*>(step3d_velocity_pair_kernel<R, TY, DX, ACC, TM>), (int)PT::bytes());
   if (e != cudaSuccess) return e;
   const Geom& g = b.base.g;
   dim3 grid((unsigned)((g.nz + b.base.zblock - 1) / b.base.zblock), (unsigned)((g.nx + kStrip - 1) / kStrip),
             (unsigned)((g.ny + TY - 1) / TY));
-  step3d_velocity_pair_kernel<R, TY, DX, ACC><<<grid, TY * 32, PT::bytes(), s>>>(b);
+  step3d_velocity_pair_kernel<R, TY, DX, ACC, TM><<<grid, TY * 32, PT::bytes(), s>>>(b);
   count_launch();
   e = cudaGetLastError();
   if (e != cudaSuccess) note_error("step kernel launch", e);
@@ -353,6 +426,10 @@ cudaError_t launch_p_d(const BatchArgs& b, cudaStream_t s) {
   bool any = false;
   for (int i = 0; i < b.nshots; ++i) any |= b.accf[i] != 0.f;
   if (!any) return launch_p<R, 16, DX, kPairNone>(b, s);
+  if (b.nshots > 2 && b.base.zblock <= (b.base.comp ? kTmemPlanesKahan : kTmemPlanes)) {
+    if (b.base.comp) return launch_p<R, 16, DX, kPairKahan, true>(b, s);
+    return launch_p<R, 16, DX, kPairSq, true>(b, s);
+  }
   if (b.base.comp) return launch_p<R, 16, DX, kPairKahan>(b, s);
   return launch_p<R, 16, DX, kPairSq>(b, s);
 }

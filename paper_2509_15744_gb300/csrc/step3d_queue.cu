@@ -135,7 +135,6 @@ step3d_velocity_queue_kernel(BatchArgs b) {
   for (int shot = 0; shot < b.nshots; ++shot) {
     const float* __restrict__ uc = b.cur[shot];
     float* __restrict__ up = b.prev[shot];
-    float* __restrict__ uout = a.u_out ? reinterpret_cast<float*>(a.u_out) : up;
     const bool acc_on = b.accf[shot] != 0;
     const float acc_sc = a.acc_scale * b.accf[shot];  // per-shot sign and on/off
 
@@ -258,7 +257,7 @@ step3d_velocity_queue_kernel(BatchArgs b) {
             const float2 n23 = __ffma2_rn(make_float2(cf.z, cf.w), l23,
                                           __ffma2_rn(two, make_float2(u.z, u.w), make_float2(-u_old.z, -u_old.w)));
             const float4 un = make_float4(n01.x, n01.y, n23.x, n23.y);
-            *reinterpret_cast<float4*>(uout + off) = un;
+            *reinterpret_cast<float4*>(up + off) = un;
             if (a.mix_a) {   // exact modes (one shot): acc += acc_scale (u_cur - u_next)(mix_a - mix_b)
               const float4 ma = *reinterpret_cast<const float4*>(a.mix_a + off);
               const float4 mb = *reinterpret_cast<const float4*>(a.mix_b + off);

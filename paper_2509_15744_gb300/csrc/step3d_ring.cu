@@ -206,7 +206,7 @@ step3d_velocity_ring_kernel(BatchArgs b) {
         un.z = fmaf(cf.z, lap[2], 2.f * u.z - u_old.z);
         un.w = fmaf(cf.w, lap[3], 2.f * u.w - u_old.w);
         const int64_t off = (int64_t)z * g.plane + row_off;
-        *reinterpret_cast<float4*>((a.u_out ? reinterpret_cast<float*>(a.u_out) : up) + off) = un;
+        *reinterpret_cast<float4*>(up + off) = un;
         if (a.mix_a) {  // exact mode (one shot): acc += acc_scale (u_cur - u_next)(mix_a - mix_b)
           const float4 ma = *reinterpret_cast<const float4*>(a.mix_a + off);
           const float4 mb = *reinterpret_cast<const float4*>(a.mix_b + off);
@@ -276,8 +276,7 @@ cudaError_t launch_step3d_batched(const BatchArgs& b, int order, cudaStream_t s)
   if (b.pair_mix) return b.nshots == 2 && b.base.g.plane < (int64_t)1 << 31 ? launch_step3d_pair(b, order, s)
                                                                            : cudaErrorInvalidValue;
   // pipeline 4 pairs the fields of a launch; a launch of one field gains nothing from it
-  if (b.base.pipeline >= 4 && b.nshots >= 2 && b.base.g.plane < (int64_t)1 << 31 && !b.base.mix_a &&
-      !b.base.u_out)
+  if (b.base.pipeline >= 4 && b.nshots >= 2 && b.base.g.plane < (int64_t)1 << 31 && !b.base.mix_a)
     return launch_step3d_pair(b, order, s);
   if (b.base.pipeline >= 3 && b.base.g.plane < (int64_t)1 << 31) return launch_step3d_queue(b, order, s);
   switch (order) {

@@ -513,7 +513,7 @@ cudaError_t launch_s_r(const StreamArgs& p, cudaStream_t s) {
 // bounded waits, no stored-history operands and no mixed (u, lambda) term.
 bool stream_supported(const BatchArgs& b) {
   const Geom& g = b.base.g;
-  return b.nshots >= 1 && b.err != nullptr && !b.pair_mix && !b.base.mix_a && !b.base.u_out && g.nz < (1 << 30) &&
+  return b.nshots >= 1 && b.err != nullptr && !b.pair_mix && !b.base.mix_a && g.nz < (1 << 30) &&
          g.ny < (1 << 30) && g.px < (1 << 30) && (g.px % kStrip) == 0;
 }
 

@@ -31,7 +31,7 @@ __device__ __forceinline__ void update_store(const StepArgs& a, int64_t off, con
   un.y = fmaf(cf.y, lap[1], 2.f * u.y - u_old.y);
   un.z = fmaf(cf.z, lap[2], 2.f * u.z - u_old.z);
   un.w = fmaf(cf.w, lap[3], 2.f * u.w - u_old.w);
-  Stor<T>::st4(reinterpret_cast<T*>(a.u_out ? a.u_out : a.u_prev) + off, un);
+  Stor<T>::st4(reinterpret_cast<T*>(a.u_prev) + off, un);
   if (a.mix_a) {  // exact mode: acc += acc_scale (u_cur - u_next)(mix_a - mix_b)
     const float4 ma = *reinterpret_cast<const float4*>(a.mix_a + off);
     const float4 mb = *reinterpret_cast<const float4*>(a.mix_b + off);

@@ -133,12 +133,12 @@ struct StepArgs {
   int64_t zblock;        // cells of the march axis per CTA (3D) / warp (2D)
   int tile_rows;         // 3D ring kernel: rows per CTA (8 or 16)
   int ring_depth;        // 3D ring kernel: planes copied ahead (2 or 3)
-  int pipeline;          // 3D FP32: 0 cp.async ring, 3 register queue, 4 two fields per pass, 5 the same with TMA tiles
+  int pipeline;          // 3D FP32: 0 cp.async ring, 3 register queue, 4 two fields per pass, 5 TMA tiles with the
+                         // accumulator in registers
   int* err;              // device error word (bounded waits)
   long long wait_limit_cycles;
   int debug_stall;
   // Exact (stored-history) mode, FP32 velocity only:
-  void* u_out;           // output level (nullable: overwrite u_prev)
   const float* mix_a;    // stored u^j (nullable): accumulate the mixed term
   const float* mix_b;    // stored u^{j-1}: acc += acc_scale (u_cur - u_next)(mix_a - mix_b)
 };

@@ -22,8 +22,10 @@ CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "tune_c
 def candidates(ndim: int, nz: int, batched: bool = False):
     """Tilings worth timing: in 2D the rows per warp; in 3D the register-queue
     kernel (pipeline 3) for one field per launch, and for batched launches also
-    the two-shots-per-pass kernels (4: cp.async staging; 5: TMA tensor tiles,
-    z-block fixed at 8)."""
+    the two-shots-per-pass kernel (4: cp.async staging; z-blocks of at most 32
+    planes, 16 with Kahan compensation, keep the accumulator in tensor memory
+    between the pairs) and the one-shot-at-a-time TMA kernel (5, z-block fixed
+    at 8)."""
     if ndim == 2:
         return [(zb, 8, 3, 0) for zb in (8, 16, 32, 64, 128) if zb <= max(8, nz)]
     out = []
@@ -33,7 +35,7 @@ def candidates(ndim: int, nz: int, batched: bool = False):
                 if zb <= max(32, nz):
                     out.append((zb, rows, depth, 3))
     if batched:
-        out += [(zb, 16, 2, 4) for zb in (32, 64, 128) if zb <= max(32, nz)]
+        out += [(zb, 16, 2, 4) for zb in (16, 32, 64, 128) if zb <= max(32, nz)]
         out += [(8, 16, 2, 5), (8, 16, 3, 5)]
     return out
 

@@ -447,6 +447,28 @@ def test_batched_pipelines_match_the_cp_async_ring(W, bc):
         assert float(c1.item()) == float(c0.item())
 
 
+@pytest.mark.parametrize("order,bc,kahan,nshots", [(8, "dirichlet", False, 5), (8, "neumann", True, 5),
+                                                  (4, "dirichlet", False, 6), (6, "dirichlet", True, 3),
+                                                  (8, "dirichlet", False, 16)])
+def test_tensor_memory_accumulator_is_bitwise_identical(W, order, bc, kahan, nshots):
+    # With more than two shots, z-blocks of at most 32 planes (16 with Kahan)
+    # keep the accumulator tile in tensor memory between the shot pairs; larger
+    # z-blocks take it through HBM.  Both must give the same bits.
+    shape = (70, 45, 200)
+    nt_list = [24 - 3 * (i % 4) for i in range(nshots)]
+    prob = make_problem(shape, order, bc, nshots=nshots, nt_list=nt_list, nrec=30, seed=71)
+    m = gpu_model(W, prob, kahan=kahan)
+    m.set_tiling(64, 16, 2, 4)
+    g0, c0, _ = m.gradient(gpu_shots(W, prob), batched=True, k=2.5)
+    for zb, depth in [(32, 2), (17, 3), (16, 2), (16, 3), (9, 2), (3, 3)]:
+        m.set_tiling(zb, 16, depth, 4)
+        g1, c1, _ = m.gradient(gpu_shots(W, prob), batched=True, k=2.5)
+        torch.cuda.synchronize()
+        assert m.check() == 0
+        assert torch.equal(g1, g0), (zb, depth)
+        assert float(c1.item()) == float(c0.item())
+
+
 def test_retired_pipelines_are_rejected(W):
     prob = make_problem((12, 14, 133), 4, "dirichlet", nt=4, nrec=5, seed=63)
     m = gpu_model(W, prob)

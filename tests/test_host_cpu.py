@@ -18,9 +18,11 @@ def test_tuner_candidates_respect_pipeline_constraints():
     assert {c[3] for c in c3} == {3}                     # one field per launch: register queue
     cb = tune.candidates(3, 512, batched=True)
     assert {c[3] for c in cb} == {3, 4, 5}
-    assert all(c[1] == 16 for c in cb if c[3] in (4, 5))   # two shots per pass: 16 rows
+    assert all(c[1] == 16 for c in cb if c[3] in (4, 5))   # 16 rows per CTA
     assert all(c[0] == 8 for c in cb if c[3] == 5)         # TMA-streamed kernel: z-block of 8
-    assert all(c[2] in (2, 3) and c[0] in (8, 32, 64, 128) for c in cb)
+    assert all(c[2] in (2, 3) and c[0] in (8, 16, 32, 64, 128) for c in cb)
+    # z-blocks that keep the accumulator in tensor memory (32; 16 with Kahan)
+    assert {(16, 16, 2, 4), (32, 16, 2, 4)} <= set(cb)
     c2 = tune.candidates(2, 300)
     assert all(c[3] == 0 and c[1] == 8 for c in c2)
     # small grids do not get z-blocks deeper than the grid
