@@ -283,10 +283,10 @@ def measured_peak():
     return 6800.0, "fallback"
 
 
-def kernel_traffic(kernel_file, workload_name):
+def kernel_traffic(kernel_file, workload_name, tiling=None):
     """dram bytes per launch of the step kernel from a committed ncu summary
-    (profiles/*_traffic.txt) taken on the current kernel source and this
-    workload, else None."""
+    (profiles/*_traffic.txt) taken on the current kernel source, this workload
+    and (when the summary names one) this tiling, else None."""
     src = open(os.path.join(ROOT, "paper_2509_15744_gb300", "csrc", kernel_file), "rb").read()
     digest = hashlib.sha256(src).hexdigest()[:16]
     for path in sorted(glob.glob(os.path.join(ROOT, "profiles", "*_traffic.txt"))):
@@ -295,6 +295,9 @@ def kernel_traffic(kernel_file, workload_name):
             if ":" in line and not line.startswith("#"):
                 k, v = line.split(":", 1)
                 vals[k.strip()] = v.strip()
+        if "tiling" in vals and tiling is not None and \
+                [int(v) for v in vals["tiling"].split(",")] != [int(v) for v in tiling]:
+            continue
         if vals.get("kernel_source_sha256_16") == digest and vals.get("workload") == workload_name:
             try:
                 return float(vals["dram_bytes_per_launch_full_size"])
@@ -530,7 +533,7 @@ def main():
                  5: "step3d_stream.cu" if mode == "batched" else "step3d_queue.cu"}[tiling[3]]
     else:
         kfile = "step_velocity.cu"
-    traffic = kernel_traffic(kfile, wl.name)
+    traffic = kernel_traffic(kfile, wl.name, tiling)
     nl = max(step_launches, 1)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "peak_source": peak_kind,

@@ -36,18 +36,23 @@ def base_workload(ndim=2):
         src = WL.flat_index(shape, 24, 20)
         rec = np.array([WL.flat_index(shape, 24, 24), WL.flat_index(shape, 20, 22), WL.flat_index(shape, 28, 18)])
         nt, order = 70, 2
+        freq = 8.0
     else:
+        # Receivers about 9 cells from the source, 5 Hz (20 cells per
+        # wavelength): a source 2 cells from the receivers and the wall is
+        # still in the near field at these grid sizes, where the oracle's own
+        # coarse-to-fine error ratio is 1.7 rather than the asymptotic 5.
         n = 20
         shape = (n, n, n)
         zz, yy, xx = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
-        v = (2000.0 + 300.0 * np.exp(-((zz - 11.0) ** 2 + (yy - 9.0) ** 2 + (xx - 10.0) ** 2) / 20.0)) \
+        v = (2000.0 + 300.0 * np.exp(-((zz - 10.0) ** 2 + (yy - 9.0) ** 2 + (xx - 10.0) ** 2) / 20.0)) \
             .astype(np.float32)
-        src = WL.flat_index(shape, 3, 10, 9)
-        rec = np.array([WL.flat_index(shape, 1, 8, 8), WL.flat_index(shape, 1, 12, 10)])
-        nt, order = 40, 4
+        src = WL.flat_index(shape, 5, 10, 9)
+        rec = np.array([WL.flat_index(shape, 14, 9, 9), WL.flat_index(shape, 12, 12, 11)])
+        nt, order, freq = 70, 2, 5.0
     return WL.Workload(name=f"smooth{ndim}d", shape=shape, h=20.0, order=order, bc="dirichlet", physics="velocity",
                        true_param=v, init_param=v, vmax=2300.0, cfl_fraction=0.5, sources=[src],
-                       receivers=[rec], nt=[nt], wavelet=WL.WaveletSpec("ricker", 8.0))
+                       receivers=[rec], nt=[nt], wavelet=WL.WaveletSpec("ricker", freq))
 
 
 def gpu_traces(W, w):

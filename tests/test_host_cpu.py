@@ -56,6 +56,11 @@ def test_traffic_record_is_used_only_for_the_current_kernel_source(tmp_path, mon
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     assert bench.kernel_traffic("k.cu", "w") == 12345.0
     assert bench.kernel_traffic("k.cu", "other workload") is None
+    (prof / "k_w2_traffic.txt").write_text(
+        f"kernel_source_sha256_16: {digest}\nworkload: w2\ntiling: 32,16,2,4\n"
+        "dram_bytes_per_launch_full_size: 777\n")
+    assert bench.kernel_traffic("k.cu", "w2", (32, 16, 2, 4)) == 777.0
+    assert bench.kernel_traffic("k.cu", "w2", [64, 16, 2, 4]) is None   # taken with another tiling
     (csrc / "k.cu").write_bytes(b"kernel v2")           # the kernel changed since the capture
     assert bench.kernel_traffic("k.cu", "w") is None
 
