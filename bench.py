@@ -50,6 +50,9 @@ def parse():
     ap.add_argument("--kahan", dest="kahan", action="store_true", default=None,
                     help="Kahan-compensated sensitivity (default: on for w4, whose configuration names it)")
     ap.add_argument("--no-kahan", dest="kahan", action="store_false")
+    ap.add_argument("--k-ratio", type=float, default=None,
+                    help="ratio r of the automatic k = r |psi| / |f_adj| (default: the library's, 1e-2 for the "
+                         "velocity form); it sets the accuracy against the exact gradient, not the speed")
     ap.add_argument("--tiling", default=None,
                     help="zblock:rows:depth:pipeline for the 3D step kernel instead of the autotuner's pick")
     ap.add_argument("--no-e2e", action="store_true")
@@ -409,7 +412,8 @@ def main():
         del mtrue, ptrue
     shots = [W.Shot(wl.sources[i], wavs[i], recs[i], observed[i]) for i in range(wl.nshots)]
     model = W.Model(param0, wl.h, dt, wl.order, wl.physics, wl.bc, kahan=args.kahan, storage=args.storage)
-    gkw = dict(objective=wl.objective, patch_sign=wl.patch_sign, batched=(mode == "batched"), mode=args.grad_mode)
+    gkw = dict(objective=wl.objective, patch_sign=wl.patch_sign, batched=(mode == "batched"), mode=args.grad_mode,
+               k_ratio=args.k_ratio)
     from paper_2509_15744_gb300 import tune
     if args.tiling:
         tiling = tuple(int(v) for v in args.tiling.split(":"))
@@ -638,7 +642,7 @@ def main():
             "config": {"workload": wl.name, "shape": list(wl.shape), "order": wl.order, "physics": wl.physics,
                        "shots": wl.nshots, "nt_total": int(sum(wl.nt)),
                        "mode": mode + (", graph replay" if use_graph else ", eager calls"),
-                       "gradient": args.grad_mode, "kahan": args.kahan,
+                       "gradient": args.grad_mode, "k_ratio": args.k_ratio, "kahan": args.kahan,
                        "storage": args.storage, "parallelism": f"replicas x{world}", "tiling": list(tiling),
                        "l2": "inputs larger than L2 (each resident grid > 129 MB)",
                        "observed_data": "true model on a 2x grid with 2x steps" if args.refined_data

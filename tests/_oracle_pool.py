@@ -41,6 +41,14 @@ def superposition(job):
     return r["K_tilde"], r["C"]
 
 
+def exact_gradient_of(job):
+    """(grad, C) of the stored-history adjoint for one shot (Sec. 2.2)."""
+    spec, src, wav, rec, nt, obs, weight = job
+    shot = O.Shot(src, np.asarray(wav, np.float64), np.asarray(rec), obs, weight)
+    c, g, _ = O.exact_gradient(_medium(spec), [shot], nt)
+    return g, c
+
+
 def pool(nproc=None):
     n = nproc or min(16, os.cpu_count() or 1)
     return mp.get_context("spawn").Pool(n)

@@ -6,7 +6,8 @@ The refined workload (workloads.refined) is run through wave_forward and
 compared with the oracle's forward on the same refined grid (the trace bar,
 1e-4); its coarse samples then converge at second order to a 4x-refined
 reference like the oracle's do, and a gradient computed from them differs
-from the same-grid (inverse-crime) gradient by the discretisation error."""
+from the same-grid (inverse-crime) gradient by as much as the oracle's
+gradients from its own two data sets differ."""
 import numpy as np
 import pytest
 import torch
@@ -100,7 +101,16 @@ def test_gradient_from_refined_data_differs_from_the_inverse_crime(W):
     g_s, c_s, _ = m.gradient([W.Shot(w.sources[0], wav, rec, torch.from_numpy(obs_same).to(DEV))], mode="symmetric")
     torch.cuda.synchronize()
     d = rel_l2(g_f.cpu().numpy(), g_s.cpu().numpy())
-    # the data differ by the discretisation error only: the gradients are close
-    # but not equal (no inverse crime)
-    assert 1e-4 < d < 0.5, d
+    # The data differ by the discretisation error only (2.7% here), yet at
+    # this starting model the gradient moves by more than its own size: the
+    # same difference computed by the oracle in FP64 from its own data.
+    ot = oracle_traces
+    o_fine, o_same = WL.coarse_samples(ot(r), 2), ot(w)
+    med = O.Medium("velocity", v0.astype(np.float64), w.h, dt, w.order, w.bc)
+    owav = O.ricker(np.arange(w.nt[0] + 1) * dt, w.wavelet.freq)
+    og = [O.exact_gradient(med, [O.Shot(w.sources[0], owav, w.receivers[0], ob)], w.nt[0])[1]
+          for ob in (o_fine, o_same)]
+    d_ref = rel_l2(og[0], og[1])
+    assert d > 1e-3, d                       # no inverse crime: the gradients differ
+    assert abs(d - d_ref) < 1e-3 * d_ref, (d, d_ref)
     assert abs(float(c_f.item()) - float(c_s.item())) > 0
