@@ -209,7 +209,9 @@ wave_status wave_model_get_block(wave_model model, int64_t* zblock);
  * neighbours in a register queue, one cp.async-staged plane tile per plane;
  * 4: two fields of a batched launch per pass, lower z neighbours in
  * registers and upper ones from the staged tiles, 16 rows only -- the
- * default; 5: the fields of a batched launch one after the other over
+ * default; with more than two fields and zblock <= 32 (<= 16 with Kahan
+ * compensation) the accumulator tile stays in the SM's tensor memory
+ * between the pairs; 5: the fields of a batched launch one after the other over
  * z-blocks of 8 planes (zblock ignored) with the accumulator of the block in
  * registers across them, the tiles copied by TMA tensor copies into an
  * mbarrier ring that holds one field's tiles, 16 rows only.  Pipelines 3-5

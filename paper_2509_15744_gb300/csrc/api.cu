@@ -170,14 +170,16 @@ static Geom make_geom(const wave_grid_desc* d) {
   return g;
 }
 
-static int64_t default_zblock(const Geom& g) {
+static int64_t default_zblock(const Geom& g, bool kahan) {
   const int64_t nstrips = (g.nx + kStrip - 1) / kStrip;
   if (g.ndim == 2) {
     // about 24 warps per SM over 152 SMs
     int64_t by = nstrips * g.ny / (152 * 24);
     return std::max<int64_t>(8, std::min<int64_t>(by, 256));
   }
-  return std::min<int64_t>(64, g.nz);
+  // the largest z-block whose accumulator tile (and compensation) fits the
+  // tensor memory of the batched two-shots-per-pass kernel
+  return std::min<int64_t>(kahan ? 16 : 32, g.nz);
 }
 
 extern "C" {
@@ -277,7 +279,7 @@ wave_status wave_model_create(const wave_grid_desc* desc, const float* param_dev
   m->param = param_dev;
   m->coef = coef;
   m->bmat = bmat;
-  m->zblock = default_zblock(g);
+  m->zblock = default_zblock(g, desc->kahan != 0);
   // untuned default: one field per launch on the register-queue kernel, two
   // or more on the two-shots-per-pass kernel (the faster of the batched ones
   // on every measured workload)
