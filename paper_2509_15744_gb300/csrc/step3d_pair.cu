@@ -44,6 +44,44 @@ __device__ __forceinline__ void pcp_wait() { asm volatile("cp.async.wait_group %
 
 enum { kPairNone = 0, kPairSq = 1, kPairKahan = 2, kPairMix = 3 };
 
+// x part of the stencil for the lane's 4 cells from A (cells x-4..x-1), B
+// (x..x+3) and C (x+4..x+7), as two cell pairs (0,1) and (2,3).  Per cell the
+// operations and their order are those of x_terms_abc (c0' u, then
+// fma(c_j, u[+j] + u[-j], s) for j = 1..r); the offsets j that keep both
+// operands of a pair in one aligned register pair (even j) run as packed
+// FP32x2 instructions, the odd ones per cell.
+// Order 2 keeps the scalar helper: its one weight c_1 = 1 turns
+// fma(c_1, s, .) into an add that the compiler may fuse with the product
+// c0' u, and every kernel must round that the same way.
+template <int R>
+__device__ __forceinline__ void x_terms_pair(const float4& A, const float4& B, const float4& C, float ndim_c0,
+                                             float2& l01, float2& l23) {
+  if constexpr (R == 1) {
+    float lap[4];
+    x_terms_abc<R>(A, B, C, lap, ndim_c0);
+    l01 = make_float2(lap[0], lap[1]);
+    l23 = make_float2(lap[2], lap[3]);
+    return;
+  }
+  const float e[12] = {A.x, A.y, A.z, A.w, B.x, B.y, B.z, B.w, C.x, C.y, C.z, C.w};
+  const float2 c0 = make_float2(ndim_c0, ndim_c0);
+  l01 = __fmul2_rn(c0, make_float2(B.x, B.y));
+  l23 = __fmul2_rn(c0, make_float2(B.z, B.w));
+#pragma unroll
+  for (int j = 1; j <= R; ++j) {
+    if (j % 2 == 0) {
+      const float2 cj = make_float2(cw<R>(j), cw<R>(j));
+      l01 = __ffma2_rn(cj, __fadd2_rn(make_float2(e[4 + j], e[5 + j]), make_float2(e[4 - j], e[5 - j])), l01);
+      l23 = __ffma2_rn(cj, __fadd2_rn(make_float2(e[6 + j], e[7 + j]), make_float2(e[6 - j], e[7 - j])), l23);
+    } else {
+      l01.x = fmaf(cw<R>(j), e[4 + j] + e[4 - j], l01.x);
+      l01.y = fmaf(cw<R>(j), e[5 + j] + e[5 - j], l01.y);
+      l23.x = fmaf(cw<R>(j), e[6 + j] + e[6 - j], l23.x);
+      l23.y = fmaf(cw<R>(j), e[7 + j] + e[7 - j], l23.y);
+    }
+  }
+}
+
 // Tensor memory (TMEM, 128 lanes x 512 columns of 32 bits per SM) holds the
 // accumulator (and Kahan compensation) tile of the CTA's z-block between the
 // shot pairs of a launch.  Warp w reaches lanes 32 (w mod 4) .. +31, one per
@@ -94,11 +132,17 @@ step3d_velocity_pair_kernel(BatchArgs b) {
   const int tid = threadIdx.x;
   const int lane = tid & 31;
   const int warp = tid >> 5;
-  const int z0 = (int)((int64_t)blockIdx.x * a.zblock);
+  // Launch order (grid built by the launcher to match): plane-major puts the
+  // x strips and then the y tiles of one z-block next to each other, so the
+  // CTAs whose halo rows overlap run at the same time and share them in L2.
+  const unsigned bzb = a.cta_order ? blockIdx.z : blockIdx.x;
+  const unsigned bxs = a.cta_order ? blockIdx.x : blockIdx.y;
+  const unsigned byt = a.cta_order ? blockIdx.y : blockIdx.z;
+  const int z0 = (int)((int64_t)bzb * a.zblock);
   const int z1 = (int)min((int64_t)z0 + a.zblock, g.nz);
   const int zs_end = z1 + R;                     // planes z0 .. zs_end-1 are staged
-  const int64_t x0 = (int64_t)blockIdx.y * kStrip;
-  const int64_t ty0 = (int64_t)blockIdx.z * TY;
+  const int64_t x0 = (int64_t)bxs * kStrip;
+  const int64_t ty0 = (int64_t)byt * TY;
   const int64_t y = ty0 + warp;
   const int64_t xl = x0 + 4 * lane;
   const bool row_valid = y < g.ny;
@@ -137,10 +181,13 @@ step3d_velocity_pair_kernel(BatchArgs b) {
       }
     }
   }
-  // x ghosts of the own row: position in the staged row, mirror source, sign
-  int fx_pos = -1, fx_src = 0;
-  float fx_sgn = 0.f;
-  if (xfix) {
+  // x ghosts of a ragged own row (nx not a multiple of the strip): lanes
+  // 0..r-1 (left end) and 8..8+r-1 (right end) write the mirror values into
+  // the staged row; computed where used, so that grids whose rows end on strip
+  // boundaries keep no registers for it
+  auto ragged_x_ghosts = [&](float* srow) {
+    int fx_pos = -1, fx_src = 0;
+    float fx_sgn = 0.f;
     int64_t gx = 0;
     if (lane < R && x0 == 0) {
       gx = -1 - lane;
@@ -153,7 +200,11 @@ step3d_velocity_pair_kernel(BatchArgs b) {
       const int64_t m = mirror_index(gx, g.nx, g.bc, &fx_sgn);
       fx_src = (int)(m - x0 + 4);
     }
-  }
+    const float val = (fx_pos >= 0 && fx_sgn != 0.f) ? fx_sgn * srow[fx_src] : 0.f;
+    __syncwarp();
+    if (fx_pos >= 0) srow[fx_pos] = val;
+    __syncwarp();
+  };
   const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
 
   __shared__ uint32_t tm_slot;
@@ -188,8 +239,10 @@ step3d_velocity_pair_kernel(BatchArgs b) {
     const float scA = a.acc_scale * fA, scB = a.acc_scale * fB;
 
     // Tiles of plane p for both fields into buffer buf; one commit group.
-    // Above the domain: the mirror source plane, positive (the wall plane
-    // of a Dirichlet box as zeros); its sign is applied when it is read.
+    // Above the domain: the mirror source plane with the mirror sign applied
+    // (the wall plane of a Dirichlet box as zeros; the planes behind it
+    // negated, copied by hand: the top r planes of the grid only), so the
+    // stencil reads every staged plane as it is.
     auto stage = [&](int p, int buf) {
       if (p < zs_end) {
         float zsg = 1.f;
@@ -200,12 +253,23 @@ step3d_velocity_pair_kernel(BatchArgs b) {
         for (int f = 0; f < 2; ++f) {
           if (f == 1 && !two) break;
           const float* src0 = (f == 0 ? ucA : ucB) + pofs;
+          float* tb = tiles + (f * NB + buf) * PT::TILE;
+          if (zsg < 0.f) {
+#pragma unroll
+            for (int k = 0; k < PT::K; ++k) {
+              const float4 v = __ldg(reinterpret_cast<const float4*>(src0 + c_off[k]));
+              if (cp_mask & (1u << k))
+                *reinterpret_cast<float4*>(tb + s_dst[k]) = c_sz[k] ? f4_scale(v, -1.f) : zero4;
+              else if (neg_mask & (1u << k))
+                *reinterpret_cast<float4*>(tb + s_dst[k]) = v;
+            }
+            continue;
+          }
           const uint32_t sb = smem0 + (uint32_t)(((f * NB) + buf) * PT::TILE) * 4u;
 #pragma unroll
           for (int k = 0; k < PT::K; ++k)
             if (cp_mask & (1u << k)) pcp16(sb + 4u * (uint32_t)s_dst[k], src0 + c_off[k], c_sz[k] & zmask);
           if (neg_mask) {
-            float* tb = tiles + (f * NB + buf) * PT::TILE;
 #pragma unroll
             for (int k = 0; k < PT::K; ++k)
               if (neg_mask & (1u << k))
@@ -215,13 +279,6 @@ step3d_velocity_pair_kernel(BatchArgs b) {
         }
       }
       pcp_commit();
-    };
-    // sign of a staged plane above the domain (1 inside)
-    auto zsign = [&](int p) -> float {
-      if (p < g.nz) return 1.f;
-      float s;
-      mirror_index(p, g.nz, g.bc, &s);
-      return s;
     };
 
     // prologue: tiles of planes z0 .. z0+D-1, lower queues of plane z0
@@ -256,19 +313,19 @@ step3d_velocity_pair_kernel(BatchArgs b) {
 
     // One field f at plane z (buffer bz; lower queue ql): new level un and
     // the centre value u the increment is taken against.
-    auto field = [&](int f, int J, int z, int bz_, bool top, const float4 (&ql)[R], const float4& u_old,
+    auto field = [&](int f, int J, int bz_, const float4 (&ql)[R], const float4& u_old,
                      const int (&zoff)[R], float4& u, float4& un) {
       float* tile = tiles + (f * NB + bz_) * PT::TILE;
       float* srow = tile + (R + warp) * kRowW;
       u = *reinterpret_cast<const float4*>(tile + own);
-      float lap[4];
+      float2 l01, l23;
       if (xfix && !xfast) {   // ragged row end: ghosts written into the staged row
-        const float val = (fx_pos >= 0 && fx_sgn != 0.f) ? fx_sgn * srow[fx_src] : 0.f;
-        __syncwarp();
-        if (fx_pos >= 0) srow[fx_pos] = val;
-        __syncwarp();
+        ragged_x_ghosts(srow);
         u = mask_row_padding(u, xl, g.nx);
+        float lap[4];
         x_terms<R>(srow, lane, lap, 3.f * cw<R>(0));
+        l01 = make_float2(lap[0], lap[1]);
+        l23 = make_float2(lap[2], lap[3]);
       } else {
         float4 xa = *reinterpret_cast<const float4*>(srow + 4 * lane);
         float4 xc = *reinterpret_cast<const float4*>(srow + 8 + 4 * lane);
@@ -276,16 +333,14 @@ step3d_velocity_pair_kernel(BatchArgs b) {
           if (lane == 0 && x0 == 0) xa = left_ghosts(u, g.bc);
           if (lane == 31 && x0 + kStrip == g.nx) xc = right_ghosts(u, g.bc);
         }
-        x_terms_abc<R>(xa, u, xc, lap, 3.f * cw<R>(0));
+        x_terms_pair<R>(xa, u, xc, 3.f * cw<R>(0), l01, l23);
       }
-      float2 l01 = make_float2(lap[0], lap[1]), l23 = make_float2(lap[2], lap[3]);
 #pragma unroll
       for (int j = 1; j <= R; ++j) {
         const float4 ym = *reinterpret_cast<const float4*>(tile + own - j * kRowW);
         const float4 yp = *reinterpret_cast<const float4*>(tile + own + j * kRowW);
         const float4 zm = ql[(J - j + R) % R];
-        float4 zp = *reinterpret_cast<const float4*>(tiles + f * NB * PT::TILE + zoff[j - 1]);
-        if (top) zp = f4_scale(zp, zsign(z + j));   // mirror sign above the domain (wall tile is zero)
+        const float4 zp = *reinterpret_cast<const float4*>(tiles + f * NB * PT::TILE + zoff[j - 1]);
         const float2 c2 = make_float2(cw<R>(j), cw<R>(j));
         l01 = __ffma2_rn(c2, __fadd2_rn(__fadd2_rn(make_float2(ym.x, ym.y), make_float2(yp.x, yp.y)),
                                         __fadd2_rn(make_float2(zm.x, zm.y), make_float2(zp.x, zp.y))), l01);
@@ -335,7 +390,6 @@ step3d_velocity_pair_kernel(BatchArgs b) {
               tm_ld4(tm_a, ac);
               if (ACC == kPairKahan) tm_ld4(tm_a + 256u, cp);
             }
-            const bool top = z + R >= g.nz;
             int zoff[R];   // own cells of planes z+1 .. z+r in the tile ring (both fields)
 #pragma unroll
             for (int j = 1; j <= R; ++j) {
@@ -344,11 +398,11 @@ step3d_velocity_pair_kernel(BatchArgs b) {
               zoff[j - 1] = bj * PT::TILE + own;
             }
             float4 ua, una;
-            field(0, J, z, bz, top, qa, oa, zoff, ua, una);
+            field(0, J, bz, qa, oa, zoff, ua, una);
             *reinterpret_cast<float4*>(upA + off) = una;
             float4 ubv = zero4, unb = zero4;
             if (two) {
-              field(1, J, z, bz, top, qb, ob, zoff, ubv, unb);
+              field(1, J, bz, qb, ob, zoff, ubv, unb);
               *reinterpret_cast<float4*>(upB + off) = unb;
             }
             if (ACC == kPairMix && acc_on) {
@@ -411,8 +465,9 @@ cudaError_t launch_p(const BatchArgs& b, cudaStream_t s) {
   cudaError_t e = set_smem_limit_once(reinterpret_cast<const void*>(step3d_velocity_pair_kernel<R, TY, DX, ACC, TM>), (int)PT::bytes());
   if (e != cudaSuccess) return e;
   const Geom& g = b.base.g;
-  dim3 grid((unsigned)((g.nz + b.base.zblock - 1) / b.base.zblock), (unsigned)((g.nx + kStrip - 1) / kStrip),
-            (unsigned)((g.ny + TY - 1) / TY));
+  const unsigned nzb = (unsigned)((g.nz + b.base.zblock - 1) / b.base.zblock);
+  const unsigned nxs = (unsigned)((g.nx + kStrip - 1) / kStrip), nyt = (unsigned)((g.ny + TY - 1) / TY);
+  const dim3 grid = b.base.cta_order ? dim3(nxs, nyt, nzb) : dim3(nzb, nxs, nyt);
   step3d_velocity_pair_kernel<R, TY, DX, ACC, TM><<<grid, TY * 32, PT::bytes(), s>>>(b);
   count_launch();
   e = cudaGetLastError();

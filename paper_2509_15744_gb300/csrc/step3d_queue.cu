@@ -69,11 +69,15 @@ step3d_velocity_queue_kernel(BatchArgs b) {
   const int tid = threadIdx.x;
   const int lane = tid & 31;
   const int warp = tid >> 5;
-  const int z0 = (int)((int64_t)blockIdx.x * a.zblock);
+  // launch order: z-block fastest, or plane-major (x strip, y tile, z-block)
+  const unsigned bzb = a.cta_order ? blockIdx.z : blockIdx.x;
+  const unsigned bxs = a.cta_order ? blockIdx.x : blockIdx.y;
+  const unsigned byt = a.cta_order ? blockIdx.y : blockIdx.z;
+  const int z0 = (int)((int64_t)bzb * a.zblock);
   const int z1 = (int)min((int64_t)z0 + a.zblock, g.nz);
   const int zs_end = z1 + R;                     // planes z0 .. zs_end-1 are staged
-  const int64_t x0 = (int64_t)blockIdx.y * kStrip;
-  const int64_t ty0 = (int64_t)blockIdx.z * TY;
+  const int64_t x0 = (int64_t)bxs * kStrip;
+  const int64_t ty0 = (int64_t)byt * TY;
   const int64_t y = ty0 + warp;
   const int64_t xl = x0 + 4 * lane;
   const bool row_valid = y < g.ny;
@@ -307,8 +311,9 @@ cudaError_t launch_q(const BatchArgs& b, cudaStream_t s) {
   cudaError_t e = set_smem_limit_once(reinterpret_cast<const void*>(step3d_velocity_queue_kernel<R, TY, DX>), (int)QT::bytes());
   if (e != cudaSuccess) return e;
   const Geom& g = b.base.g;
-  dim3 grid((unsigned)((g.nz + b.base.zblock - 1) / b.base.zblock), (unsigned)((g.nx + kStrip - 1) / kStrip),
-            (unsigned)((g.ny + TY - 1) / TY));
+  const unsigned nzb = (unsigned)((g.nz + b.base.zblock - 1) / b.base.zblock);
+  const unsigned nxs = (unsigned)((g.nx + kStrip - 1) / kStrip), nyt = (unsigned)((g.ny + TY - 1) / TY);
+  const dim3 grid = b.base.cta_order ? dim3(nxs, nyt, nzb) : dim3(nzb, nxs, nyt);
   step3d_velocity_queue_kernel<R, TY, DX><<<grid, TY * 32, QT::bytes(), s>>>(b);
   count_launch();
   e = cudaGetLastError();

@@ -135,6 +135,8 @@ struct StepArgs {
   int ring_depth;        // 3D ring kernel: planes copied ahead (2 or 3)
   int pipeline;          // 3D FP32: 0 cp.async ring, 3 register queue, 4 two fields per pass, 5 TMA tiles with the
                          // accumulator in registers
+  int cta_order;         // 3D pipelines 3 and 4: 0 z-block fastest in launch order, 1 plane-major (x strip fastest,
+                         // then y tile, then z-block)
   int* err;              // device error word (bounded waits)
   long long wait_limit_cycles;
   int debug_stall;

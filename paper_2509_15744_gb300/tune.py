@@ -1,10 +1,12 @@
 """Autotuner for the step kernel's tiling, with a JSON cache.
 
 The tiling (`wave_model_set_tiling`: z-block depth, rows per CTA, ring
-depth, pipeline) changes speed only, never results.  `tune()` times a short forward
-pass of the given shots with each candidate (CUDA events inside libwave,
-`wave_timing_*`), keeps the fastest, applies it to the model and caches it
-under a key of (dims, shape, order, physics, storage, Kahan, shots per launch).
+depth, pipeline) and the CTA launch order (`wave_model_set_schedule`) change
+speed only, never results.  `tune()` times a short gradient call of the given
+shots with each tiling candidate in the default (plane-major) order (CUDA
+events inside libwave, `wave_timing_*`), keeps the fastest, times that tiling
+once more in the other order, applies the faster and caches the choice under
+a key of (dims, shape, order, physics, storage, Kahan, shots per launch).
 """
 from __future__ import annotations
 
@@ -68,8 +70,10 @@ def tune(model: W.Model, shots: Sequence[W.Shot], steps: int = 12, batched: bool
     key = _key(model, batch)
     cache = _load() if use_cache else {}
     if key in cache:
-        best = tuple(cache[key])
+        entry = list(cache[key])
+        best = tuple(entry[:4])
         model.set_tiling(*best)
+        model.set_schedule(entry[4] if len(entry) > 4 else 1)
         return best
     dev = model.param.device
     probe = []
@@ -78,21 +82,28 @@ def tune(model: W.Model, shots: Sequence[W.Shot], steps: int = 12, batched: bool
         probe.append(W.Shot(s.src, s.wavelet[:n + 1].contiguous(), s.rec,
                             None if s.observed is None else s.observed[:, :n + 1].contiguous()))
     nz = model.shape[0]
-    results = []
-    for cand in candidates(len(model.shape), nz, batched and batch > 1):
+
+    def time_one(cand, order):
         model.set_tiling(*cand)
+        model.set_schedule(order)
         model.gradient(probe, batched=batched, k=1.0)          # warm-up (and attribute setup)
         torch.cuda.synchronize(dev)
         W.timing_enable(True)
         model.gradient(probe, batched=batched, k=1.0)
         ms, n, _ = W.timing_read()
         W.timing_enable(False)
-        results.append((ms / max(n, 1), cand))
         if verbose:
-            print(f"tiling {cand}: {ms / max(n, 1):.4f} ms per step launch")
-    best = min(results)[1]
+            print(f"tiling {cand} order {order}: {ms / max(n, 1):.4f} ms per step launch")
+        return ms / max(n, 1)
+
+    results = [(time_one(cand, 1), cand) for cand in candidates(len(model.shape), nz, batched and batch > 1)]
+    t_best, best = min(results)
+    order = 1
+    if len(model.shape) == 3 and best[3] in (3, 4) and time_one(best, 0) < t_best:
+        order = 0
     model.set_tiling(*best)
+    model.set_schedule(order)
     if use_cache:
-        cache[key] = list(best)
+        cache[key] = list(best) + [order]
         _save(cache)
     return best

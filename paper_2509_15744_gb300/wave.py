@@ -75,6 +75,7 @@ _model_destroy = _sig("wave_model_destroy", _st, _vp)
 _model_set_block = _sig("wave_model_set_block", _st, _vp, C.c_int64)
 _model_get_block = _sig("wave_model_get_block", _st, _vp, C.POINTER(C.c_int64))
 _model_set_tiling = _sig("wave_model_set_tiling", _st, _vp, C.c_int64, _i32, _i32, _i32)
+_model_set_schedule = _sig("wave_model_set_schedule", _st, _vp, _i32)
 _model_check = _sig("wave_model_check", _st, _vp, _vp)
 _model_set_param = _sig("wave_model_set_param", _st, _vp, _vp, _vp)
 _model_set_debug = _sig("wave_model_set_debug", _st, _vp, _i32, C.c_int64)
@@ -246,6 +247,7 @@ class Model:
         self.desc = d
         self.h, self.dt, self.order, self.physics, self.bc = h, dt, order, physics, bc
         self.storage, self.kahan = storage, kahan
+        self.cta_order = 1   # the library's default launch order (plane-major)
         nbytes = _sz(0)
         _check(_model_ws(C.byref(d), C.byref(nbytes)), "wave_model_workspace_size")
         self._ws = _workspace(nbytes.value, self.param.device)
@@ -276,6 +278,11 @@ class Model:
     def set_tiling(self, zblock: int, tile_rows: int = 8, ring_depth: int = 3, pipeline: int = 0):
         _check(_model_set_tiling(self._h, int(zblock), int(tile_rows), int(ring_depth), int(pipeline)),
                "wave_model_set_tiling")
+
+    def set_schedule(self, cta_order: int = 1):
+        """Launch order of the 3D step CTAs: 0 z-block fastest, 1 plane-major (wave_model_set_schedule)."""
+        _check(_model_set_schedule(self._h, int(cta_order)), "wave_model_set_schedule")
+        self.cta_order = int(cta_order)
 
     def set_metrics(self, on: bool = True):
         """Record per-pass CUDA events in later gradient calls (wave_model_set_metrics)."""

@@ -469,6 +469,39 @@ def test_tensor_memory_accumulator_is_bitwise_identical(W, order, bc, kahan, nsh
         assert float(c1.item()) == float(c0.item())
 
 
+@pytest.mark.parametrize("order,kahan,nshots", [(8, False, 5), (8, True, 4), (8, False, 2), (2, True, 3),
+                                                (4, False, 3), (6, True, 3)])
+def test_cta_order_is_bitwise_identical(W, order, kahan, nshots):
+    # The launch order of the CTAs changes which halo rows are found in L2,
+    # never what a cell computes: on the register-queue and the
+    # two-shots-per-pass kernels (accumulator through HBM and in tensor
+    # memory) both orders give the same bits, and at order 8 they are the bits
+    # of the cp.async ring kernel.
+    shape = (40, 37, 259)
+    nt_list = [20 - 2 * (i % 3) for i in range(nshots)]
+    prob = make_problem(shape, order, "dirichlet", nshots=nshots, nt_list=nt_list, nrec=25, seed=73)
+    m = gpu_model(W, prob, kahan=kahan)
+    m.set_tiling(8, 8, 3, 0)
+    g0, c0, _ = m.gradient(gpu_shots(W, prob), batched=True, k=2.5)
+    for tiling in [(16, 16, 2, 4), (64, 16, 2, 4), (9, 16, 3, 4), (16, 16, 3, 3), (8, 8, 2, 3)]:
+        m.set_tiling(*tiling)
+        m.set_schedule(0)
+        ga, ca, _ = m.gradient(gpu_shots(W, prob), batched=True, k=2.5)
+        m.set_schedule(1)
+        gb, cb, _ = m.gradient(gpu_shots(W, prob), batched=True, k=2.5)
+        torch.cuda.synchronize()
+        assert m.check() == 0
+        assert torch.equal(ga, gb), tiling
+        assert float(ca.item()) == float(cb.item())
+        if order == 8:
+            assert torch.equal(gb, g0), tiling
+            assert float(cb.item()) == float(c0.item())
+        else:
+            assert rel_l2(gb.cpu().numpy(), g0.cpu().numpy()) < GRAD_TOL, tiling
+    with pytest.raises(W.WaveError):
+        m.set_schedule(2)
+
+
 def test_retired_pipelines_are_rejected(W):
     prob = make_problem((12, 14, 133), 4, "dirichlet", nt=4, nrec=5, seed=63)
     m = gpu_model(W, prob)

@@ -165,3 +165,9 @@ def test_metrics_calls_validate_on_the_host(lib):
     assert W._metrics_read(None, C.byref(m)) == 1
     assert W._set_metrics(None, 1) == 1
     assert W._model_set_param(None, None, None) == 1
+
+
+def test_schedule_setter_validates_on_the_host(lib):
+    # a null model is rejected before anything else is looked at
+    assert lib.wave_model_set_schedule(None, 1) == 1
+    assert lib.wave_model_set_schedule(None, 0) == 1
