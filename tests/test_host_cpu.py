@@ -76,6 +76,12 @@ def test_bench_options():
         sys.argv = ["bench.py"]
         a = bench.parse()
         assert a.gpus == 1 and a.warmup >= 3 and a.workload == "w2" and a.impl == "ours"
+        assert a.cta_order is None   # the tuner's pick
+        sys.argv = ["bench.py", "--cta-order", "0"]
+        assert bench.parse().cta_order == 0
+        sys.argv = ["bench.py", "--cta-order", "2"]
+        with pytest.raises(SystemExit):
+            bench.parse()
     finally:
         sys.argv = old
 
@@ -99,3 +105,85 @@ def test_smooth_field_is_a_sum_of_separable_modes():
     np.testing.assert_allclose(f, ref, rtol=2e-5)
     w4 = WL.workload4(n=32, nt=10)
     assert w4.nshots == 4 and len(set(w4.sources)) == 4 and w4.receivers[0].size == 32 * 32
+
+
+class _FakeModel:
+    """Stands in for wave.Model in the tuner: records the tiling and launch
+    order it is given and the gradient calls made with them."""
+
+    def __init__(self, shape, kahan=False):
+        import torch
+        self.shape, self.order, self.physics, self.storage, self.kahan = shape, 8, "velocity", "f32", kahan
+        self.param = torch.zeros(1)
+        self.tiling, self.cta_order, self.calls = None, 1, []
+
+    def set_tiling(self, *t):
+        self.tiling = tuple(t)
+
+    def set_schedule(self, order):
+        self.cta_order = int(order)
+
+    def gradient(self, shots, **kw):
+        self.calls.append((self.tiling, self.cta_order))
+
+
+def _fake_tuner(monkeypatch, tmp_path, times):
+    """The tuner with its timing read from `times[(tiling, order)]` (ms per launch)."""
+    import torch
+    from paper_2509_15744_gb300 import tune
+    state = {}
+    monkeypatch.setattr(tune, "CACHE", str(tmp_path / "tune_cache.json"))
+    monkeypatch.setattr(tune.torch.cuda, "synchronize", lambda *a, **k: None)
+    monkeypatch.setattr(tune.W, "timing_enable", lambda on: None)
+    monkeypatch.setattr(tune.W, "timing_read",
+                        lambda: (times.get((state["m"].tiling, state["m"].cta_order), 100.0), 1, 0.0))
+    shot = tune.W.Shot(0, torch.zeros(31), torch.zeros(4, dtype=torch.int64), None)
+    return tune, state, [shot, shot]
+
+
+def test_tuner_keeps_the_faster_launch_order_of_its_best_tiling(monkeypatch, tmp_path):
+    pytest.importorskip("torch")
+    best = (32, 16, 2, 4)
+    times = {(best, 1): 7.70, (best, 0): 7.60, ((16, 16, 2, 4), 1): 8.0}
+    tune, state, shots = _fake_tuner(monkeypatch, tmp_path, times)
+    m = state["m"] = _FakeModel((64, 64, 64))
+    assert tune.tune(m, shots, batched=True) == best
+    assert m.tiling == best and m.cta_order == 0
+    # every candidate was timed in the default (plane-major) order, the best one also in the other
+    assert {o for t, o in m.calls if t != best} == {1}
+    assert (best, 0) in m.calls
+    # the cache holds the order; a second call applies it without timing anything
+    import json
+    assert json.load(open(tune.CACHE))[tune._key(m, 2)] == list(best) + [0]
+    m2 = state["m"] = _FakeModel((64, 64, 64))
+    assert tune.tune(m2, shots, batched=True) == best
+    assert m2.calls == [] and m2.cta_order == 0 and m2.tiling == best
+
+
+def test_tuner_stays_plane_major_when_it_is_faster(monkeypatch, tmp_path):
+    pytest.importorskip("torch")
+    best = (16, 16, 2, 4)
+    times = {(best, 1): 6.0, (best, 0): 6.5}
+    tune, state, shots = _fake_tuner(monkeypatch, tmp_path, times)
+    m = state["m"] = _FakeModel((64, 64, 64), kahan=True)
+    assert tune.tune(m, shots, batched=True) == best
+    assert m.cta_order == 1
+
+
+def test_tuner_reads_cache_entries_without_an_order(monkeypatch, tmp_path):
+    pytest.importorskip("torch")
+    import json
+    tune, state, shots = _fake_tuner(monkeypatch, tmp_path, {})
+    m = state["m"] = _FakeModel((64, 64, 64))
+    m.cta_order = 0
+    json.dump({tune._key(m, 2): [64, 16, 2, 4]}, open(tune.CACHE, "w"))
+    assert tune.tune(m, shots, batched=True) == (64, 16, 2, 4)
+    assert m.cta_order == 1 and m.calls == []
+
+
+def test_tuner_tries_no_launch_order_in_2d(monkeypatch, tmp_path):
+    pytest.importorskip("torch")
+    tune, state, shots = _fake_tuner(monkeypatch, tmp_path, {((16, 8, 3, 0), 1): 1.0})
+    m = state["m"] = _FakeModel((64, 64))
+    assert tune.tune(m, shots) == (16, 8, 3, 0)
+    assert all(o == 1 for _, o in m.calls)
