@@ -52,6 +52,9 @@ int main(void) {
   /* the static-scratch misfit rejects sizes beyond its limit on the host */
   double out = 0.0;
   CHECK(wave_misfit_static(NULL, NULL, (int64_t)1 << 40, 1.0, 1.0, &out, NULL) != WAVE_OK);
+  /* tuning setters reject a missing model */
+  CHECK(wave_model_set_schedule(NULL, 1) == WAVE_EINVAL);
+  CHECK(wave_model_set_tiling(NULL, 32, 16, 2, 4) == WAVE_EINVAL);
   if (failures == 0) printf("c abi host checks: ok\n");
   return failures == 0 ? 0 : 1;
 }
