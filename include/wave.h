@@ -226,7 +226,8 @@ wave_status wave_model_set_tiling(wave_model model, int64_t zblock, int32_t tile
  * each other, so the CTAs whose staged halo rows overlap run at the same time
  * and read those rows from L2 rather than HBM.  It matters once the CTAs of
  * one z-block outnumber the resident ones (1024^3 with z-blocks of 16
- * planes: 3.4% less time per launch); other values: WAVE_EINVAL. */
+ * planes: 3.4% less time per launch).  A grid of more than 65535 z-blocks
+ * launches in order 0 whatever the setting.  Other values: WAVE_EINVAL. */
 wave_status wave_model_set_schedule(wave_model model, int32_t cta_order);
 /* Waits for `stream` and reports whether a bounded device wait of a step
  * kernel gave up since the last check (WAVE_ETIMEOUT; the results of that

@@ -266,6 +266,14 @@ static cudaError_t launch_ring_r(const BatchArgs& a, cudaStream_t s) {
 }
 
 cudaError_t launch_step3d_batched(const BatchArgs& b, int order, cudaStream_t s) {
+  // The plane-major launch order of pipelines 3 and 4 puts the z-blocks in
+  // gridDim.z (at most 65535); a grid with more z-blocks launches in the
+  // z-block-fastest order (z-blocks in gridDim.x), which computes the same.
+  if (b.base.cta_order && b.base.zblock > 0 && (b.base.g.nz + b.base.zblock - 1) / b.base.zblock > 65535) {
+    BatchArgs c = b;
+    c.base.cta_order = 0;
+    return launch_step3d_batched(c, order, s);
+  }
   // Pipelines: 0 this cp.async ring (64-bit offsets: any grid, the fallback);
   // 3 register queue in z; 4 two fields per pass; 5 two fields per pass with
   // TMA tensor tiles.  A launch of one field goes to the register queue from
